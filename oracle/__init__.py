@@ -84,6 +84,10 @@ def _load():
                                            ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32,
                                            _dp, _dp]
         lib.oracle_backproject.restype = ctypes.c_int
+        lib.oracle_count_segments.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32, _i64p,
+                                              ctypes.c_int64, _ip]
+        lib.oracle_count_segments.restype = ctypes.c_int
         lib.oracle_hu_to_mu.argtypes = [_i16p, ctypes.c_int64, ctypes.c_double, _dp]
         lib.oracle_hu_to_mu.restype = None
         for name in ("oracle_round_bf16", "oracle_round_f16"):
@@ -237,6 +241,27 @@ def backproject(shape_zyx, spacing, det, poses, grad_out):
                            float(dh), float(dw), _ptr(poses, ctypes.c_float), int(B), _ptr(g, ctypes.c_double),
                            _ptr(out, ctypes.c_double))
     return out
+
+
+def count_segments(shape_zyx, spacing, det, poses, pixels=None):
+    """Segments per ray (consecutive pairs of the sorted crossing list, Eq. 4): (B, H, W) or (B, npix) int32."""
+    lib = _load()
+    sdr, H, W, dh, dw = det
+    nz, ny, nx = shape_zyx
+    n = np.array([nx, ny, nz], dtype=np.int32)
+    delta = np.array(spacing, dtype=np.float64)
+    poses = _c(poses, np.float32).reshape(-1, 6)
+    B = poses.shape[0]
+    if pixels is None:
+        npix, pix_ptr = H * W, None
+    else:
+        pixels = _c(pixels, np.int64).reshape(-1)
+        npix, pix_ptr = pixels.size, _ptr(pixels, ctypes.c_int64)
+    out = np.zeros((B, npix), np.int32)
+    lib.oracle_count_segments(_ptr(n, ctypes.c_int32), _ptr(delta, ctypes.c_double), float(sdr), int(H), int(W),
+                              float(dh), float(dw), _ptr(poses, ctypes.c_float), int(B), pix_ptr, int(npix),
+                              _ptr(out, ctypes.c_int32))
+    return out.reshape(B, H, W) if pixels is None else out
 
 
 def hu_to_mu(hu, mu_water: float):

@@ -121,6 +121,7 @@ static int cmp_crossing(const void* a, const void* b) {
 }
 
 static double voxel_value(const int32_t n[3], const float* vol, const int64_t idx[3]) {
+  if (!vol) return 0.0;
   for (int a = 0; a < 3; ++a)
     if (idx[a] < 0 || idx[a] >= n[a]) return 0.0;
   return (double)vol[(idx[2] * n[1] + idx[1]) * (int64_t)n[0] + idx[0]];
@@ -392,6 +393,33 @@ int oracle_pose_grad(const int32_t n[3], const double delta[3], const float* vol
     }
   free(E);
   free(J);
+  return 0;
+}
+
+/* Number of segments (consecutive pairs of the sorted list of Eq. 4) per ray,
+ * zero-length ones included; 0 when the ray misses. out[b][q] like oracle_render. */
+static void count_one(void* ctx, const int64_t idx[3], double len) {
+  (void)idx;
+  (void)len;
+  *(int32_t*)ctx += 1;
+}
+int oracle_count_segments(const int32_t n[3], const double delta[3], double sdr, int32_t H, int32_t W, double dh,
+                          double dw, const float* poses, int32_t B, const int64_t* pix, int64_t npix, int32_t* out) {
+  if (!pix) npix = (int64_t)H * W;
+  crossing_t* list = alloc_list(n);
+  for (int32_t bi = 0; bi < B; ++bi) {
+    double pose[6];
+    for (int k = 0; k < 6; ++k) pose[k] = (double)poses[6 * bi + k];
+    for (int64_t q = 0; q < npix; ++q) {
+      int64_t flat = pix ? pix[q] : q;
+      double s[3], p[3];
+      oracle_ray_endpoints(pose, sdr, H, W, dh, dw, (int32_t)(flat / W), (int32_t)(flat % W), s, p);
+      int32_t c = 0;
+      siddon_ray(n, delta, NULL, s, p, NULL, NULL, list, count_one, &c);
+      out[(int64_t)bi * npix + q] = c;
+    }
+  }
+  free(list);
   return 0;
 }
 

@@ -177,3 +177,30 @@ def test_segment_inside_the_box():
     data = np.full((4, 4, 4), 0.5, np.float32)
     V = oracle.Volume(data, (1, 1, 1))
     assert oracle.siddon_ray(V, [-1.2, 0.1, 0.1], [0.8, 0.1, 0.1]) == pytest.approx(1.0, abs=1e-12)
+
+
+def test_segment_count_is_voxels_crossed():
+    # with no coincident crossings, segments == voxels the segment passes through with positive length
+    rng = np.random.default_rng(16)
+    n = np.array([5, 4, 6])
+    sp = np.array([1.1, 0.9, 1.3])
+    b = -0.5 * n * sp
+    det = (30.0, 3, 4, 0.7, 0.9)
+    poses = np.array([[0.3, -0.2, 0.1, 0.4, -0.3, 0.2], [1.1, 0.5, -0.7, -0.2, 0.6, -0.1]], np.float32)
+    counts = oracle.count_segments(n[::-1], sp, det, poses)
+    for bi in range(2):
+        for h in range(3):
+            for w in range(4):
+                s, p = oracle.ray_endpoints(poses[bi].astype(np.float64), *det, h, w)
+                d = p - s
+                crossed = 0
+                for k in range(n[2]):
+                    for j in range(n[1]):
+                        for i in range(n[0]):
+                            lo = b + np.array([i, j, k]) * sp
+                            hi = lo + sp
+                            t0, t1 = (lo - s) / d, (hi - s) / d
+                            tl = max(0.0, np.max(np.minimum(t0, t1)))
+                            th = min(1.0, np.min(np.maximum(t0, t1)))
+                            crossed += th - tl > 1e-12
+                assert counts[bi, h, w] == crossed
