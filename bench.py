@@ -1,0 +1,312 @@
+"""Throughput benchmark: Siddon DRR forward + pose gradient on one GB300.
+
+Workload (the headline configuration): a 512x512x133 chest-CT-shaped volume
+(seeded int16 HU phantom mapped to FP32 attenuation, spacing 0.703 x 0.703 x
+2.5 mm), a 200x200 detector at 1.4 mm, SDR 510 mm, a batch of 16 random poses.
+One step = the whole hot path for that batch: pose setup, the fused Siddon
+forward with per-ray pose Jacobian (DRR + dE/d eta), and the deterministic
+reduction of a seeded upstream gradient to dL/d pose.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gray-s fwd & fwd+pose-grad at 512x512x133 CT, 200x200 det; served p50/p99 ms"
+UNIT = "Grays/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_inputs():
+    from paper_2208_12737_gb300 import inputs
+    cfg = inputs.CT
+    hu = inputs.ct_volume_hu()
+    poses = inputs.random_poses(cfg["batch"], seed=cfg["pose_seed"])
+    g = inputs.upstream_grad((cfg["batch"], cfg["detector"].height, cfg["detector"].width), seed=3)
+    return cfg, hu, poses, g
+
+
+def cpu_oracle_sample(cfg, hu, poses, seconds_target=10.0, threads=0):
+    """Time the FP64 oracle (forward + per-ray pose Jacobian) on a bounded pixel sample."""
+    import oracle
+    from paper_2208_12737_gb300 import inputs
+    f32 = lambda x: float(np.float32(x))
+    mu = oracle.hu_to_mu(hu, inputs.MU_WATER).astype(np.float32)
+    ov = oracle.Volume(mu, tuple(f32(s) for s in cfg["spacing"]))
+    d = cfg["detector"]
+    det = (f32(d.sdr), d.height, d.width, f32(d.delta_h), f32(d.delta_w))
+    rng = np.random.default_rng(123)
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
+    # calibrate on a small sample, then size the timed sample to about seconds_target
+    npix = 64
+    t0 = time.perf_counter()
+    oracle.render(ov, det, poses, pixels=rng.integers(0, d.height * d.width, npix), jacobian=True, threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rate = poses.shape[0] * npix / dt
+    npix = int(min(d.height * d.width, max(64, rate * seconds_target / poses.shape[0])))
+    pix = rng.choice(d.height * d.width, size=npix, replace=False)
+    t0 = time.perf_counter()
+    oracle.render(ov, det, poses, pixels=pix, jacobian=True, threads=cores)
+    dt = time.perf_counter() - t0
+    rays = poses.shape[0] * npix
+    return {"value": rays / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{npix} random pixels x {poses.shape[0]} poses of the 512x512x133/200x200 workload "
+                      f"(fwd + per-ray pose Jacobian, FP64), {dt:.1f} s"}, dt, rays
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    cfg, hu, poses, _ = workload_inputs()
+    per = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        cb, dt, rays = cpu_oracle_sample(cfg, hu, poses, seconds_target=max(1.0, 60.0 / (args.steps + args.warmup)))
+        if i >= args.warmup:
+            per.append(cb["value"])
+            base = cb
+    value = statistics.median(per)
+    base["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "volume": "512x512x133 HU->FP32", "detector": "200x200 @1.4mm",
+                       "batch": cfg["batch"], "sample": base["sample"]},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2208_12737_gb300 import build
+    build.build()
+    from paper_2208_12737_gb300 import drr
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    cfg, hu, poses_np, g_np = workload_inputs()
+    det = cfg["detector"]
+    B, H, W = cfg["batch"], det.height, det.width
+    rays = B * H * W
+    vol = drr.Volume(hu, cfg["spacing"], hu=True, storage=args.storage)
+    poses = torch.from_numpy(poses_np).to(dev)
+    g = torch.from_numpy(g_np).to(dev)
+    E = torch.empty((B, H, W), device=dev)
+    J = torch.empty((B, 6, H, W), device=dev)
+
+    def step():
+        drr.render(vol, det, poses, jacobian=True, out=E, jac=J)
+        return drr.render_backward(vol, det, poses, g, jac=J)
+
+    def fwd():
+        drr.render(vol, det, poses, out=E)
+
+    # inputs larger than L2 are not the case here (the volume is meant to stay L2-resident
+    # between renders); L2 is flushed before every timed step instead, outside the events.
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    seg = drr.count_segments(vol, det, poses).to(torch.int64).sum().item()  # outside the timed region
+    elem = {"f32": 4, "bf16": 2, "f16": 2}[args.storage]
+
+    for _ in range(args.warmup):
+        step()
+        fwd()
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        for i in range(k):
+            flush.fill_(float(i))
+            starts[i].record()
+            fn()
+            ends[i].record()
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = drr.launch_count()
+    drr.profile_reset()
+    drr.profile_enable(True)
+    t0 = time.perf_counter()
+    step_ms = timed(step, args.steps)
+    wall = time.perf_counter() - t0
+    drr.profile_enable(False)
+    launches = drr.launch_count() - launches0
+    kern_ms, kern_n = drr.profile_read("siddon_fwd_jac")
+    red_ms, red_n = drr.profile_read("jac_reduce")
+    fwd_ms = timed(fwd, args.steps)
+    # end-to-end through the public API: pinned host poses in, DRR + pose gradient out
+    poses_h = torch.from_numpy(poses_np).pin_memory()
+    E_h = torch.empty((B, H, W), dtype=torch.float32).pin_memory()
+    G_h = torch.empty((B, 6), dtype=torch.float32).pin_memory()
+    poses_d = torch.empty_like(poses)
+
+    def e2e():
+        poses_d.copy_(poses_h, non_blocking=True)
+        drr.render(vol, det, poses_d, jacobian=True, out=E, jac=J)
+        G = drr.render_backward(vol, det, poses_d, g, jac=J)
+        E_h.copy_(E, non_blocking=True)
+        G_h.copy_(G, non_blocking=True)
+
+    e2e_ms = timed(e2e, args.steps)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    drr.profile_reset()
+
+    ms = statistics.mean(step_ms)
+    worst = torch.tensor([ms, statistics.mean(fwd_ms), statistics.mean(e2e_ms)], device=dev)
+    if dist:
+        dist.all_reduce(worst, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms, fms, ems = worst.tolist()
+    if rank != 0:
+        return
+    value = world * rays / (ms * 1e-3) / 1e9
+    peaks, which = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # dominant kernel: the fused forward + Jacobian walk; algorithmic work per launch
+    k_ms = kern_ms / max(kern_n, 1)
+    ops_per_seg = 8  # 3-way min (2), length (1), accumulate (1), next crossing (1), Jacobian weight and sums (3)
+    achieved = seg * ops_per_seg / (k_ms * 1e-3) / 1e12
+    peak_alu = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x max SM clock, tera-ops/s
+    gather_gbs = (seg * elem + rays * 4 * 7) / (k_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"{args.storage}-storage/f32-accum",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "volume": "512x512x133 int16 HU -> FP32 /mm, 0.703x0.703x2.5 mm",
+                   "detector": "200x200 @ 1.4 mm, SDR 510 mm", "batch": B, "rays_per_step": rays,
+                   "segments_per_step": int(seg), "storage": args.storage,
+                   "step": "pose setup + fused Siddon fwd with per-ray pose Jacobian + g.J reduction",
+                   "l2": "flushed (512 MB write) before every timed step, outside the timed events"},
+        "fwd_only": {"value": world * rays / (fms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": fms},
+        "drrs_per_s": world * B / (ms * 1e-3),
+        "segments_per_s": world * seg / (ms * 1e-3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tops/s",
+                     "frac": achieved / peak_alu, "traffic": None,
+                     "kernel": "siddon_fwd_jac", "kernel_ms": k_ms,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({which} sm_max)",
+                     "gathered_gbs": gather_gbs},
+        "e2e": {"value": world * rays / (ems * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": B * 6 * 4,
+                "d2h_bytes_per_step": B * H * W * 4 + B * 6 * 4},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if not args.no_cpu_baseline:
+        cb, _, _ = cpu_oracle_sample(cfg, hu, poses_np, seconds_target=args.cpu_seconds)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * drr.h -- C ABI of libdrr, a GB300 (sm_103a) library for differentiable
+ * digitally reconstructed radiographs by Siddon ray tracing
+ * (Gopalakrishnan & Golland, arXiv 2208.12737).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Geometry (Sec. 2.2, 2.4 and Eq. 1-3 of the paper, with these readings):
+ *      volume box [b, b + n*delta] with b = -(n*delta)/2 (centred at the origin),
+ *      voxel (i,j,k) is the half-open box [b + (i,j,k)*delta, b + (i+1,j+1,k+1)*delta);
+ *      pose eta = (rz, ry, rx, tx, ty, tz) in radians / mm,
+ *      R = Rz(rz) Ry(ry) Rx(rx), source s = R (rho, 0, 0) + t with rho = sdr/2,
+ *      pixel (h, w) centre p = R (-rho, (w - (W-1)/2) dw, (h - (H-1)/2) dh) + t.
+ *    The output E(h,w) is the radiologic path length of Eq. (2):
+ *      E = |p - s| * sum_m (alpha_{m+1} - alpha_m) V[voxel at the segment midpoint],
+ *    with alpha clipped to the volume (Sec. 2.3) and clamped to [0, 1].
+ *  - Volumes are passed x fastest: a C array of shape (nz, ny, nx).
+ *  - Pointers named *_dev are caller-owned CUDA device memory on the current
+ *    device; the library never frees them.  Host pointers are only read during
+ *    the call.
+ *  - Calls taking a `cuda_stream` (a cudaStream_t, NULL = legacy default
+ *    stream) enqueue their work on it and return without synchronising.
+ *    Argument errors are reported synchronously; errors raised by device work
+ *    surface as DRR_ERR_CUDA from a later call or from drr_stream_check().
+ *  - Every call returns a drr_status; on failure drr_last_error() gives a
+ *    message (thread-local, valid until the next failing call on that thread).
+ *  - Empty work (B == 0, H*W == 0) and non-positive sizes or spacings are
+ *    DRR_ERR_INVALID.  Non-finite poses give NaN outputs, not an error.
+ */
+#ifndef DRR_H_
+#define DRR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct drr_volume_s* drr_volume;
+typedef struct drr_server_s* drr_server;
+
+typedef enum {
+  DRR_OK = 0,
+  DRR_ERR_INVALID = 1,   /* bad argument */
+  DRR_ERR_OOM = 2,       /* device allocation failed, or a server budget is exhausted */
+  DRR_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  DRR_ERR_TIMEOUT = 4,   /* a bounded wait ran out */
+  DRR_ERR_BUSY = 5,      /* the object is still referenced (e.g. a volume held by a server) */
+  DRR_ERR_NOT_FOUND = 6, /* unknown ticket */
+  DRR_ERR_DEVICE = 7,    /* a kernel reported an error through its status word */
+  DRR_ERR_CANCELLED = 8  /* the request was cancelled */
+} drr_status;
+
+typedef enum {
+  DRR_F32 = 0,   /* float32 */
+  DRR_BF16 = 1,  /* bfloat16 (storage only) */
+  DRR_F16 = 2,   /* IEEE half (storage only; values are stored times a power-of-two scale) */
+  DRR_I16_HU = 3 /* int16 Hounsfield units (input only) */
+} drr_dtype;
+
+/* Detector of Sec. 2.4: source-to-detector distance sdr (= 2 rho), height x
+ * width pixels of spacing delta_h x delta_w (mm). */
+typedef struct {
+  float sdr_mm;
+  int32_t height;
+  int32_t width;
+  float delta_h_mm;
+  float delta_w_mm;
+} drr_detector;
+
+/* Options for drr_volume_create.  Zero-initialised fields take defaults. */
+typedef struct {
+  drr_dtype storage;  /* DRR_F32 (default), DRR_BF16 or DRR_F16 */
+  float hu_mu_water;  /* attenuation of water in /mm for DRR_I16_HU input:
+                         mu = max(0, mu_water (1 + HU/1000)); 0 -> 0.02 */
+  int32_t layout;     /* 0 = default; 1 = padded linear (x fastest);
+                         2 = bricked (brick edges below) */
+  int32_t brick[3];   /* brick edge in voxels along x, y, z (powers of two, <= 64);
+                         used when layout == 2 */
+} drr_volume_options;
+
+/* ---- volumes (Sec. 2.2: the CT volume V and its spacing) ---------------- */
+
+/* Upload and convert a volume into device-resident storage.
+ *  data           : nz*ny*nx values of src_dtype, x fastest; host memory if
+ *                   data_on_device == 0, device memory otherwise.  Only read.
+ *  src_dtype      : DRR_F32 (attenuation, /mm) or DRR_I16_HU (mapped to /mm).
+ *  nx, ny, nz     : voxel counts (>= 1); dx, dy, dz: spacing in mm (> 0).
+ *  opt            : NULL for defaults.
+ *  cuda_stream    : stream for the upload/conversion; the call synchronises
+ *                   it before returning (the volume is ready on return).
+ *  out            : receives the handle; destroy with drr_volume_destroy.
+ * FP16 storage multiplies values by scale = 2^(14 - e) where max(V) = m 2^e,
+ * m in [0.5, 1) (scale 1 when max(V) == 0); outputs are divided by it again.
+ * Errors: DRR_ERR_INVALID, DRR_ERR_OOM, DRR_ERR_CUDA. */
+drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype src_dtype, int32_t nx,
+                             int32_t ny, int32_t nz, float dx_mm, float dy_mm, float dz_mm,
+                             const drr_volume_options* opt, void* cuda_stream, drr_volume* out);
+
+/* Release a volume.  DRR_ERR_BUSY while a server still references it.
+ * The caller must ensure no enqueued render still uses it. */
+drr_status drr_volume_destroy(drr_volume v);
+
+/* Query a volume: dims (nx, ny, nz), spacing (mm), storage dtype, the storage
+ * scale (1 except FP16) and the device bytes it holds.  Any out pointer may be NULL. */
+drr_status drr_volume_info(drr_volume v, int32_t dims[3], float spacing[3], drr_dtype* storage,
+                           float* storage_scale, size_t* device_bytes);
+
+/* ---- rendering (Eq. 2 for every detector pixel, Sec. 2.3) ---------------- */
+
+/* Forward DRR for B poses.
+ *  poses_dev   : [B][6] float32 (rz, ry, rx radians; tx, ty, tz mm).
+ *  drr_out_dev : [B][H][W] float32, overwritten with E.
+ *  jac_out_dev : NULL, or [B][6][H][W] float32 (planar) overwritten with
+ *                dE/d eta_k per pixel (Sec. 2.4 gradient, voxel lookup held
+ *                fixed), for a later drr_render_backward.
+ * Errors: DRR_ERR_INVALID, DRR_ERR_OOM, DRR_ERR_CUDA. */
+drr_status drr_render(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
+                      float* drr_out_dev, float* jac_out_dev, void* cuda_stream);
+
+/* Reverse pass (Sec. 2.4: gradient of a loss through the DRR).
+ *  grad_drr_dev    : [B][H][W] float32 upstream gradient dL/dE.
+ *  jac_dev         : [B][6][H][W] from drr_render, or NULL to re-trace the
+ *                    rays and form the Jacobian on the fly.
+ *  grad_pose_dev   : NULL, or [B][6] float32, overwritten with
+ *                    sum_{h,w} dL/dE(h,w) dE(h,w)/d eta (deterministic:
+ *                    fixed-order reduction, FP64 second pass).
+ *  grad_volume_dev : NULL, or [nz][ny][nx] float32 dL/dV (attenuation units),
+ *                    ACCUMULATED into (back-projection with atomic adds; the
+ *                    summation order, hence the last bits, is not deterministic).
+ * At least one of grad_pose_dev / grad_volume_dev must be non-NULL.
+ * Errors: DRR_ERR_INVALID, DRR_ERR_OOM, DRR_ERR_CUDA. */
+drr_status drr_render_backward(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
+                               const float* grad_drr_dev, const float* jac_dev, float* grad_pose_dev,
+                               float* grad_volume_dev, void* cuda_stream);
+
+/* Ray setup alone (Sec. 2.4): for every pose and pixel write the source s
+ * and pixel centre p in world coordinates, rays_out_dev = [B][H][W][6] float32
+ * (sx, sy, sz, px, py, pz).  Used to test the geometry kernel. */
+drr_status drr_ray_setup(const drr_detector* det, const float* poses_dev, int32_t B, float* rays_out_dev,
+                         void* cuda_stream);
+
+/* Number of Siddon segments (Eq. 2 terms) of every ray: segments_out_dev =
+ * [B][H][W] int32, 0 for rays that miss.  A segment is the part of a ray
+ * inside one voxel between consecutive plane crossings (Eq. 4), counting the
+ * zero-length ones produced when two crossings coincide. */
+drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
+                              int32_t* segments_out_dev, void* cuda_stream);
+
+/* ---- profiling (no counterpart in the paper) ------------------------------ */
+
+/* While enabled, every kernel launch is bracketed by CUDA events recorded on
+ * its stream.  Kernel names: "pose_setup", "siddon_fwd", "siddon_fwd_jac",
+ * "siddon_pose_grad", "jac_reduce", "pose_grad_finalize", "siddon_backproject",
+ * "count_segments". */
+drr_status drr_profile_enable(int32_t on);
+/* Synchronise the recorded events and return the summed device time (ms) and
+ * the number of launches of one kernel since the last reset. */
+drr_status drr_profile_read(const char* kernel, double* total_ms, int64_t* launches);
+/* Drop all recorded events. */
+drr_status drr_profile_reset(void);
+/* Total kernel launches issued by the library since it was loaded. */
+int64_t drr_launch_count(void);
+
+/* Synchronise a stream and report any pending device error as DRR_ERR_CUDA. */
+drr_status drr_stream_check(void* cuda_stream);
+
+/* Thread-local message for the last failing call (never NULL). */
+const char* drr_last_error(void);
+
+/* Library version string. */
+const char* drr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRR_H_ */

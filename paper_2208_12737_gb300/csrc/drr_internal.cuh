@@ -1,0 +1,77 @@
+// Internal types shared by the libdrr kernels and the C-ABI layer.
+// Nothing here is part of the public ABI (include/drr.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace drr {
+
+// Pixel tiling of the ray kernels: a 256-thread block covers 32 x 8 pixels,
+// each warp an 8 (columns) x 4 (rows) tile so that its 32 rays are spatial
+// neighbours and their voxel gathers share cache lines.
+constexpr int kThreads = 256;
+constexpr int kTileW = 32;
+constexpr int kTileH = 8;
+constexpr int kWarpTileW = 8;
+constexpr int kWarpTileH = 4;
+
+enum StorageType : int { kF32 = 0, kBF16 = 1, kF16 = 2 };
+
+// Per-pose ray geometry (Sec. 2.4), written by the pose-setup kernel.
+// Positions and directions are in voxel-index units of the volume:
+// u = (x - b) / delta per axis, so voxel i spans [i, i+1).
+struct PoseGeom {
+  double u0[3];   // source position u(s)
+  double un[3];   // n_a - u0[a] (distance of the far face, voxel units)
+  double g00[3];  // direction (p - s) / delta at pixel (h=0, w=0)
+  double gw[3];   // change of the direction per detector column
+  double gh[3];   // change of the direction per detector row
+  // Chain-rule terms for the pose Jacobian, world units (mm), j = angle index:
+  float S[3][3];   // dR/d eta_j * s_c
+  float Q[3][3];   // dR/d eta_j * (p_c(0,0) - s_c)
+  float Wv[3][3];  // dR/d eta_j * (0, dw, 0)
+  float Hv[3][3];  // dR/d eta_j * (0, 0, dh)
+};
+
+// A device-resident volume as the kernels see it.
+struct VolumeDev {
+  const void* data;  // storage (padded: one zero voxel on each side of every axis)
+  int n[3];          // logical voxel counts nx, ny, nz
+  float delta[3];    // spacing (mm)
+  int dtype;         // StorageType
+  float out_scale;   // E multiplier undoing the storage scale (FP16)
+  int stride[3];     // element strides of the padded layout along x, y, z
+  int origin;        // element offset of voxel (0,0,0)
+  int64_t elems;     // padded element count
+};
+
+struct DetDev {
+  int H, W;
+  float sdr, dh, dw;
+};
+
+// Launchers (drr_kernels.cu).  All enqueue on `stream` and return the
+// cudaGetLastError() of the launch.
+cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, const VolumeDev* vd, PoseGeom* out,
+                              cudaStream_t stream);
+cudaError_t launch_ray_setup(const float* poses, int B, const DetDev& det, float* rays, cudaStream_t stream);
+cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
+                          cudaStream_t stream);
+// Pose gradient by re-tracing (jac == nullptr) or from a stored Jacobian.
+// partials must hold B * pose_grad_blocks(det) * 6 floats.
+int pose_grad_blocks(const DetDev& det, bool from_jacobian);
+cudaError_t launch_pose_grad_partials(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
+                                      const float* grad_drr, const float* jac, float* partials, cudaStream_t stream);
+cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream);
+cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, int* counts,
+                                  cudaStream_t stream);
+cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
+                               const float* grad_drr, float* grad_vol, cudaStream_t stream);
+// Volume ingest.
+cudaError_t launch_abs_max(const void* src, int src_dtype, int64_t count, float mu_water, unsigned int* out_bits,
+                           cudaStream_t stream);
+cudaError_t launch_ingest(const void* src, int src_dtype, float mu_water, const VolumeDev& vd, void* dst,
+                          float scale, cudaStream_t stream);
+
+}  // namespace drr

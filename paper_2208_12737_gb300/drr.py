@@ -1,0 +1,321 @@
+"""ctypes binding of libdrr (include/drr.h) and a torch.autograd.Function.
+
+Argument marshalling only: torch supplies device memory and the current
+CUDA stream; every step of the DRR computation runs in libdrr's kernels.
+The library must have been built (``paper_2208_12737_gb300.build.build()``);
+if it is missing, loading raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdrr.so")
+
+DRR_F32, DRR_BF16, DRR_F16, DRR_I16_HU = 0, 1, 2, 3
+_STATUS = {0: "DRR_OK", 1: "DRR_ERR_INVALID", 2: "DRR_ERR_OOM", 3: "DRR_ERR_CUDA", 4: "DRR_ERR_TIMEOUT",
+           5: "DRR_ERR_BUSY", 6: "DRR_ERR_NOT_FOUND", 7: "DRR_ERR_DEVICE", 8: "DRR_ERR_CANCELLED"}
+STORAGE = {"f32": DRR_F32, "bf16": DRR_BF16, "f16": DRR_F16}
+
+# Every symbol include/drr.h declares (checked by the CPU tests).
+EXPORTS = (
+    "drr_volume_create", "drr_volume_destroy", "drr_volume_info", "drr_render", "drr_render_backward",
+    "drr_ray_setup", "drr_count_segments", "drr_profile_enable", "drr_profile_read", "drr_profile_reset",
+    "drr_launch_count", "drr_stream_check", "drr_last_error", "drr_version",
+)
+
+
+class DrrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class drr_detector(ctypes.Structure):
+    _fields_ = [("sdr_mm", ctypes.c_float), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("delta_h_mm", ctypes.c_float), ("delta_w_mm", ctypes.c_float)]
+
+
+class drr_volume_options(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("hu_mu_water", ctypes.c_float), ("layout", ctypes.c_int32),
+                ("brick", ctypes.c_int32 * 3)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+
+
+def load(path: str = LIB_PATH):
+    """Load libdrr.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FileNotFoundError(f"libdrr not built: {path} is missing (run paper_2208_12737_gb300.build.build())")
+        lib = ctypes.CDLL(path)
+        lib.drr_last_error.restype = ctypes.c_char_p
+        lib.drr_last_error.argtypes = []
+        lib.drr_version.restype = ctypes.c_char_p
+        lib.drr_version.argtypes = []
+        lib.drr_volume_create.argtypes = [_vp, _i32, _i32, _i32, _i32, _i32, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_float, ctypes.POINTER(drr_volume_options), _vp,
+                                          ctypes.POINTER(_vp)]
+        lib.drr_volume_destroy.argtypes = [_vp]
+        lib.drr_volume_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_size_t)]
+        lib.drr_render.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp, _vp]
+        lib.drr_render_backward.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp, _vp, _vp, _vp]
+        lib.drr_ray_setup.argtypes = [ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp]
+        lib.drr_stream_check.argtypes = [_vp]
+        lib.drr_count_segments.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp]
+        lib.drr_profile_enable.argtypes = [_i32]
+        lib.drr_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64)]
+        lib.drr_profile_reset.argtypes = []
+        lib.drr_launch_count.argtypes = []
+        for name in EXPORTS:
+            if name not in ("drr_last_error", "drr_version"):
+                getattr(lib, name).restype = ctypes.c_int
+        lib.drr_launch_count.restype = ctypes.c_int64
+        _lib = lib
+        return lib
+
+
+def check(status: int):
+    if status != 0:
+        msg = _lib.drr_last_error().decode() if _lib is not None else ""
+        raise DrrError(status, msg)
+
+
+def detector(det) -> drr_detector:
+    """From an inputs.Detector, a (sdr, H, W, dh, dw) tuple or a drr_detector."""
+    if isinstance(det, drr_detector):
+        return det
+    if hasattr(det, "as_tuple"):
+        det = det.as_tuple()
+    sdr, H, W, dh, dw = det
+    return drr_detector(float(sdr), int(H), int(W), float(dh), float(dw))
+
+
+def _stream_ptr(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch.Tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Volume:
+    """A device-resident CT volume (drr_volume_create / drr_volume_destroy).
+
+    data: (nz, ny, nx) float32 attenuation (/mm) or int16 HU (``hu=True``), as a numpy
+    array (uploaded from host) or a CUDA tensor.  spacing = (dx, dy, dz) mm.
+    """
+
+    def __init__(self, data, spacing, storage: str = "f32", hu: bool = False, mu_water: float = 0.02,
+                 layout: int = 0, stream=None):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.handle = ctypes.c_void_p()
+        src_dtype = DRR_I16_HU if hu else DRR_F32
+        want = np.int16 if hu else np.float32
+        if isinstance(data, torch.Tensor):
+            tdt = torch.int16 if hu else torch.float32
+            t = data.to(tdt).contiguous()
+            if not t.is_cuda:
+                t = t.cuda()
+            ptr = ctypes.c_void_p(t.data_ptr())
+            on_dev = 1
+            shape = tuple(t.shape)
+            self._keep = t
+        else:
+            arr = np.ascontiguousarray(data, dtype=want)
+            ptr = arr.ctypes.data_as(ctypes.c_void_p)
+            on_dev = 0
+            shape = arr.shape
+            self._keep = arr
+        if len(shape) != 3:
+            raise ValueError("volume must be (nz, ny, nx)")
+        nz, ny, nx = shape
+        opt = drr_volume_options(STORAGE[storage], float(mu_water) if hu else 0.0, int(layout), (0, 0, 0))
+        torch.cuda.init()
+        check(lib.drr_volume_create(ptr, on_dev, src_dtype, nx, ny, nz, float(spacing[0]), float(spacing[1]),
+                                    float(spacing[2]), ctypes.byref(opt), _stream_ptr(stream),
+                                    ctypes.byref(self.handle)))
+        self._keep = None
+        self.shape_zyx = (nz, ny, nx)
+        self.spacing = tuple(float(s) for s in spacing)
+        self.storage = storage
+
+    def info(self):
+        dims = (_i32 * 3)()
+        sp = (ctypes.c_float * 3)()
+        st = _i32()
+        sc = ctypes.c_float()
+        nb = ctypes.c_size_t()
+        check(self._lib.drr_volume_info(self.handle, dims, sp, ctypes.byref(st), ctypes.byref(sc), ctypes.byref(nb)))
+        return dict(dims=tuple(dims), spacing=tuple(sp), storage=st.value, scale=sc.value, bytes=nb.value)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            check(self._lib.drr_volume_destroy(self.handle))
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self.handle is not None and self.handle.value:
+                self._lib.drr_volume_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def render(volume: Volume, det, poses, jacobian: bool = False, out=None, jac=None, stream=None):
+    """E (B, H, W) float32 on the poses' device; with jacobian=True also dE/d eta (B, 6, H, W)."""
+    import torch
+    lib = load()
+    d = detector(det)
+    B = poses.shape[0]
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
+    if out is None:
+        out = torch.empty((B, d.height, d.width), device=poses.device, dtype=torch.float32)
+    op = _dev_ptr(out, torch.float32, (B, d.height, d.width), "out")
+    jp = None
+    if jacobian:
+        if jac is None:
+            jac = torch.empty((B, 6, d.height, d.width), device=poses.device, dtype=torch.float32)
+        jp = _dev_ptr(jac, torch.float32, (B, 6, d.height, d.width), "jac")
+    check(lib.drr_render(volume.handle, ctypes.byref(d), pp, B, op, jp, _stream_ptr(stream)))
+    return (out, jac) if jacobian else out
+
+
+def render_backward(volume: Volume, det, poses, grad_drr, jac=None, pose_grad: bool = True, grad_volume=None,
+                    stream=None):
+    """Returns dL/d eta (B, 6) (or None) and accumulates dL/dV into grad_volume if given."""
+    import torch
+    lib = load()
+    d = detector(det)
+    B = poses.shape[0]
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
+    gp = _dev_ptr(grad_drr, torch.float32, (B, d.height, d.width), "grad_drr")
+    jp = _dev_ptr(jac, torch.float32, (B, 6, d.height, d.width), "jac") if jac is not None else None
+    gpose = torch.empty((B, 6), device=poses.device, dtype=torch.float32) if pose_grad else None
+    gpp = _dev_ptr(gpose, torch.float32, (B, 6), "grad_pose") if pose_grad else None
+    gvp = _dev_ptr(grad_volume, torch.float32, volume.shape_zyx, "grad_volume") if grad_volume is not None else None
+    check(lib.drr_render_backward(volume.handle, ctypes.byref(d), pp, B, gp, jp, gpp, gvp, _stream_ptr(stream)))
+    return gpose
+
+
+def ray_setup(det, poses, stream=None):
+    """Source and pixel centres (B, H, W, 6) = (sx, sy, sz, px, py, pz) from the ray-setup kernel."""
+    import torch
+    lib = load()
+    d = detector(det)
+    B = poses.shape[0]
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
+    rays = torch.empty((B, d.height, d.width, 6), device=poses.device, dtype=torch.float32)
+    check(lib.drr_ray_setup(ctypes.byref(d), pp, B, ctypes.c_void_p(rays.data_ptr()), _stream_ptr(stream)))
+    return rays
+
+
+def count_segments(volume: Volume, det, poses, stream=None):
+    """Per-ray Siddon segment counts (B, H, W) int32."""
+    import torch
+    lib = load()
+    d = detector(det)
+    B = poses.shape[0]
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
+    out = torch.empty((B, d.height, d.width), device=poses.device, dtype=torch.int32)
+    check(lib.drr_count_segments(volume.handle, ctypes.byref(d), pp, B, ctypes.c_void_p(out.data_ptr()),
+                                 _stream_ptr(stream)))
+    return out
+
+
+def profile_enable(on: bool = True):
+    check(load().drr_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    check(load().drr_profile_reset())
+
+
+def profile_read(kernel: str):
+    """(total device ms, launches) of one kernel since the last reset."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    check(load().drr_profile_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def launch_count() -> int:
+    return int(load().drr_launch_count())
+
+
+def stream_check(stream=None):
+    lib = load()
+    check(lib.drr_stream_check(_stream_ptr(stream)))
+
+
+def _autograd():
+    import torch
+
+    class DRRFunction(torch.autograd.Function):
+        """poses (B, 6) -> DRR (B, H, W); backward gives dL/d poses via the fused Jacobian."""
+
+        @staticmethod
+        def forward(ctx, poses, volume, det):
+            E, J = render(volume, det, poses.contiguous(), jacobian=True)
+            ctx.volume = volume
+            ctx.det = det
+            ctx.save_for_backward(poses, J)
+            return E
+
+        @staticmethod
+        def backward(ctx, grad):
+            poses, J = ctx.saved_tensors
+            g = render_backward(ctx.volume, ctx.det, poses.contiguous(), grad.contiguous().float(), jac=J)
+            return g, None, None
+
+    return DRRFunction
+
+
+_fn = None
+
+
+def drr(volume: Volume, det, poses):
+    """Differentiable DRR: E = drr(volume, det, poses) with gradients to poses."""
+    global _fn
+    if _fn is None:
+        _fn = _autograd()
+    return _fn.apply(poses, volume, det)
+
+
+class DRR:
+    """Callable renderer bound to a volume and detector: ``DRR(vol, det)(poses)``."""
+
+    def __init__(self, volume: Volume, det):
+        self.volume = volume
+        self.det = det
+
+    def __call__(self, poses):
+        return drr(self.volume, self.det, poses)

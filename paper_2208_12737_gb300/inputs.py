@@ -44,7 +44,9 @@ def _rotation(rng) -> np.ndarray:
 
 
 def _paint_ellipsoid(vol, spacing, centre_mm, semi_mm, rot, value, mode="add"):
-    """Add (or set) `value` inside an ellipsoid, voxel centres tested, bbox-restricted."""
+    """Add (or set) `value` inside an ellipsoid, voxel centres tested, bbox-restricted.
+
+    `rot` has the ellipsoid axes as columns (world = rot @ local)."""
     nz, ny, nx = vol.shape
     dx, dy, dz = spacing
     ext = np.array([nx * dx, ny * dy, nz * dz])
@@ -56,12 +58,15 @@ def _paint_ellipsoid(vol, spacing, centre_mm, semi_mm, rot, value, mode="add"):
     hi = np.clip(hi, 0, [nx, ny, nz])
     if np.any(hi <= lo):
         return
-    xs = b[0] + (np.arange(lo[0], hi[0]) + 0.5) * dx - centre_mm[0]
-    ys = b[1] + (np.arange(lo[1], hi[1]) + 0.5) * dy - centre_mm[1]
-    zs = b[2] + (np.arange(lo[2], hi[2]) + 0.5) * dz - centre_mm[2]
-    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
-    pts = np.stack([X, Y, Z], axis=-1) @ rot  # coordinates in the ellipsoid frame
-    inside = np.sum((pts / np.asarray(semi_mm)) ** 2, axis=-1) <= 1.0
+    xs = (b[0] + (np.arange(lo[0], hi[0]) + 0.5) * dx - centre_mm[0]).astype(np.float32)
+    ys = (b[1] + (np.arange(lo[1], hi[1]) + 0.5) * dy - centre_mm[1]).astype(np.float32)
+    zs = (b[2] + (np.arange(lo[2], hi[2]) + 0.5) * dz - centre_mm[2]).astype(np.float32)
+    q = np.zeros((hi[2] - lo[2], hi[1] - lo[1], hi[0] - lo[0]), np.float32)
+    for k in range(3):  # local coordinate k = sum_a world_a * rot[a, k]
+        u = (zs[:, None, None] * np.float32(rot[2, k]) + ys[None, :, None] * np.float32(rot[1, k])
+             + xs[None, None, :] * np.float32(rot[0, k]))
+        q += (u / np.float32(semi_mm[k])) ** 2
+    inside = q <= 1.0
     sub = vol[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
     if mode == "add":
         sub[inside] += value
@@ -121,7 +126,7 @@ def ct_phantom_hu(shape_zyx=(133, 512, 512), spacing=(0.703, 0.703, 2.5), seed=2
         rot = np.array([[np.cos(ang + np.pi / 2), -np.sin(ang + np.pi / 2), 0],
                         [np.sin(ang + np.pi / 2), np.cos(ang + np.pi / 2), 0], [0, 0, 1]]).T
         _paint_ellipsoid(hu, spacing, c, semi, rot, float(rng.uniform(1000, 2000)), mode="set")
-    noise = rng.normal(0.0, 10.0, size=shape_zyx).astype(np.float32)
+    noise = rng.standard_normal(size=shape_zyx, dtype=np.float32) * np.float32(10.0)
     hu = np.where(body_mask, hu + noise, hu)
     return np.clip(np.rint(hu), -1000, 2000).astype(np.int16)
 
