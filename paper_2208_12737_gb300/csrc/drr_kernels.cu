@@ -186,22 +186,35 @@ __device__ __forceinline__ void block_sum6(float v[6], float (*sm)[6]) {
   }
 }
 
-template <int MODE, int DT>
-__device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gscale,
-                                          float* __restrict__ gvol, RayResult& res) {
-  res.F = 0.f;
-  res.nseg = 0;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) res.J[k] = 0.f;
+// Per-ray state after the FP64 setup: everything the FP32 walk needs.
+struct RaySetup {
+  int nseg;        // segments = plane crossings + 1 (0: the ray misses)
+  int off;         // element offset of the entry voxel (padded layout)
+  int ient[3];     // entry voxel index per axis
+  int cnt[3];      // plane crossings per axis between the entry and exit voxels
+  int step[3];     // signed element stride per axis
+  int ea, xa;      // axis of the entry / exit plane, -1 when clamped to alpha = 0 / 1
+  float first[3];  // alpha (from the entry) of each axis' first crossing; kNoCrossing if none
+  float delta[3];  // alpha between consecutive planes of each axis
+  float span;      // alpha_max - alpha_min
+  double amin;     // absolute alpha of the entry
+  float d[3];      // p - s in mm
+};
 
-  // Direction p - s in voxel units for this pixel (FP64).
+// FP64 clip (Sec. 2.3, clamped to [0, 1]), entry/exit voxels and first
+// crossings.  tieD receives FP64 first[3], delta[3] for exact tie ordering.
+// Returns 1 for a hit, 0 when the ray misses, -1 for non-finite geometry.
+__device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg, int h, int w, RaySetup& r,
+                                         double* tieD) {
   double g[3];
+  bool finite = true;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) g[a] = fma(static_cast<double>(h), pg.gh[a], fma(static_cast<double>(w), pg.gw[a], pg.g00[a]));
-
-  // Clip to the volume box: a_min = max of per-axis entries, a_max = min of
-  // exits (Sec. 2.3), clamped to [0, 1].  An axis with g == 0 constrains
-  // nothing if the ray lies inside its slab [0, n), else the ray misses.
+  for (int a = 0; a < 3; ++a) {
+    g[a] = fma(static_cast<double>(h), pg.gh[a], fma(static_cast<double>(w), pg.gw[a], pg.g00[a]));
+    finite = finite && isfinite(g[a]) && isfinite(pg.u0[a]);
+  }
+  r.nseg = 0;
+  if (!finite) return -1;
   double amin = 0.0, amax = 1.0, rg[3];
   int ea = -1, xa = -1;
   bool hit = true;
@@ -218,20 +231,22 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
       if (!(pg.u0[a] >= 0.0 && pg.un[a] > 0.0)) hit = false;
     }
   }
-  if (!hit || !(amin < amax)) return;
-
-  // Entry and exit voxels, crossing counts and the first crossing of each
-  // axis measured from the entry point (FP64, then FP32).
-  int ient[3], cnt[3];
-  float a_first[3], a_step[3];
+  if (!hit || !(amin < amax)) return 0;
+  r.ea = ea;
+  r.xa = xa;
+  r.amin = amin;
+  int total = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int n = vd.n[a];
+    r.d[a] = static_cast<float>(g[a] * static_cast<double>(vd.delta[a]));
     if (g[a] == 0.0) {
-      ient[a] = min(max(static_cast<int>(floor(pg.u0[a])), 0), n - 1);
-      cnt[a] = 0;
-      a_first[a] = kNoCrossing;
-      a_step[a] = 0.f;
+      r.ient[a] = min(max(static_cast<int>(floor(pg.u0[a])), 0), n - 1);
+      r.cnt[a] = 0;
+      r.first[a] = kNoCrossing;
+      r.delta[a] = 0.f;
+      r.step[a] = vd.stride[a];
+      if (tieD) { tieD[a] = 4.0; tieD[3 + a] = 0.0; }
       continue;
     }
     const bool up = g[a] > 0.0;
@@ -244,139 +259,302 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
     else i1 = up ? static_cast<int>(ceil(ux)) - 1 : static_cast<int>(floor(ux));
     i0 = min(max(i0, 0), n - 1);
     i1 = min(max(i1, 0), n - 1);
-    ient[a] = i0;
-    cnt[a] = max(up ? i1 - i0 : i0 - i1, 0);
+    r.ient[a] = i0;
+    r.cnt[a] = max(up ? i1 - i0 : i0 - i1, 0);
+    total += r.cnt[a];
     const double plane = static_cast<double>(up ? i0 + 1 : i0);
-    a_first[a] = cnt[a] > 0 ? static_cast<float>((plane - ue) * rg[a]) : kNoCrossing;
-    a_step[a] = static_cast<float>(fabs(rg[a]));
+    const double f64 = (plane - ue) * rg[a];
+    r.first[a] = r.cnt[a] > 0 ? static_cast<float>(f64) : kNoCrossing;
+    r.delta[a] = static_cast<float>(fabs(rg[a]));
+    r.step[a] = up ? vd.stride[a] : -vd.stride[a];
+    if (tieD) { tieD[a] = f64; tieD[3 + a] = fabs(rg[a]); }
   }
-  const float span = static_cast<float>(amax - amin);
-  const int nseg = cnt[0] + cnt[1] + cnt[2] + 1;
-  res.nseg = nseg;
-  if (MODE == kCount) return;
+  r.span = static_cast<float>(amax - amin);
+  r.nseg = total + 1;
+  r.off = vd.origin + r.ient[0] * vd.stride[0] + r.ient[1] * vd.stride[1] + r.ient[2] * vd.stride[2];
+  return 1;
+}
 
-  int off = vd.origin + ient[0] * vd.stride[0] + ient[1] * vd.stride[1] + ient[2] * vd.stride[2];
-  const int sx = g[0] > 0.0 ? vd.stride[0] : -vd.stride[0];
-  const int sy = g[1] > 0.0 ? vd.stride[1] : -vd.stride[1];
-  const int sz = g[2] > 0.0 ? vd.stride[2] : -vd.stride[2];
-
-  // Linear index into an unpadded (nz, ny, nx) gradient volume (back-projection).
-  int lin = 0, lx = 0, ly = 0, lz = 0;
-  unsigned int nvox = 0;
-  float gL = 0.f;
-  if (MODE == kBackproject) {
-    lin = ient[0] + vd.n[0] * (ient[1] + vd.n[1] * ient[2]);
-    lx = g[0] > 0.0 ? 1 : -1;
-    ly = g[1] > 0.0 ? vd.n[0] : -vd.n[0];
-    lz = g[2] > 0.0 ? vd.n[0] * vd.n[1] : -(vd.n[0] * vd.n[1]);
-    nvox = static_cast<unsigned int>(vd.n[0] * vd.n[1] * vd.n[2]);
-    const float dx = static_cast<float>(g[0]) * vd.delta[0], dy = static_cast<float>(g[1]) * vd.delta[1],
-                dz = static_cast<float>(g[2]) * vd.delta[2];
-    gL = gscale * sqrtf(dx * dx + dy * dy + dz * dz);
-  }
-
-  float ax = a_first[0], ay = a_first[1], az = a_first[2];
+// Forward walk (Sec. 2.2 Siddon-Jacobs, Eq. 2): sum (a_{m+1} - a_m) V over the
+// ray.  Crossings are ordered by their FP32 alphas; two crossings closer than
+// FP32 resolution change E only by that resolution times the density step.
+// The next voxel is loaded one iteration ahead of its use.  An axis whose
+// planes are used up can be picked once more only within FP32 rounding of the
+// exit, and that step lands in the zero padding.
+template <int DT>
+__device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetup& r) {
+  float ax = r.first[0], ay = r.first[1], az = r.first[2];
   float kx = 0.f, ky = 0.f, kz = 0.f;
+  int off = r.off;
+  float v = Voxel<DT>::load(vd.data, off);
   float acc = 0.f, ac = 0.f;
-  // Jacobian bookkeeping: each plane crossing with weight w = V_before - V_after
-  // contributes d alpha / d(s, p) (Sec. 2.4); sums are kept per axis:
-  //   Gs[a] = sum w,   As[a] = sum w * alpha_rel.
-  float vprev = 0.f;
-  int pa = ea;  // axis of the crossing that starts the current segment (-1: none)
-  float Gs0 = 0.f, Gs1 = 0.f, Gs2 = 0.f, As0 = 0.f, As1 = 0.f, As2 = 0.f;
-
-  for (int m = 0; m < nseg; ++m) {
-    const float an = fminf(fminf(ax, ay), fminf(az, span));
-    const float len = an - ac;
-    if (MODE != kBackproject) {
-      const float v = Voxel<DT>::load(vd.data, off);
-      acc = fmaf(len, v, acc);
-      if (MODE == kFwdJac || MODE == kPoseGrad) {
-        const float wgt = vprev - v;
-        const float wa = wgt * ac;
-        if (pa == 0) { Gs0 += wgt; As0 += wa; }
-        else if (pa == 1) { Gs1 += wgt; As1 += wa; }
-        else if (pa == 2) { Gs2 += wgt; As2 += wa; }
-        vprev = v;
-      }
-    } else {
-      if (static_cast<unsigned int>(lin) < nvox) atomicAdd(gvol + lin, gL * len);
-    }
+  for (int m = 1; m < r.nseg; ++m) {
+    // branch-free step of the axis with the nearest crossing
+    const float an = fminf(fminf(ax, ay), az);
+    const bool bx = ax == an;
+    const bool by = !bx && ay == an;
+    const bool bz = !bx && !by;
+    off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
+    if (bx) kx += 1.f;
+    if (by) ky += 1.f;
+    if (bz) kz += 1.f;
+    ax = fmaf(kx, r.delta[0], r.first[0]);
+    ay = fmaf(ky, r.delta[1], r.first[1]);
+    az = fmaf(kz, r.delta[2], r.first[2]);
+    const float vn = Voxel<DT>::load(vd.data, off);
+    acc = fmaf(an - ac, v, acc);
     ac = an;
-    if (ax <= an) {
-      off += sx; kx += 1.f; ax = fmaf(kx, a_step[0], a_first[0]); pa = 0;
-      if (MODE == kBackproject) lin += lx;
-    } else if (ay <= an) {
-      off += sy; ky += 1.f; ay = fmaf(ky, a_step[1], a_first[1]); pa = 1;
-      if (MODE == kBackproject) lin += ly;
-    } else {
-      off += sz; kz += 1.f; az = fmaf(kz, a_step[2], a_first[2]); pa = 2;
-      if (MODE == kBackproject) lin += lz;
-    }
+    v = vn;
   }
-  res.F = acc;
+  return fmaf(r.span - ac, v, acc);
+}
 
-  if (MODE == kFwdJac || MODE == kPoseGrad) {
-    // Exit crossing (weight V_last - 0) unless the exit is the clamp a = 1.
-    if (xa == 0) { Gs0 += vprev; As0 += vprev * span; }
-    else if (xa == 1) { Gs1 += vprev; As1 += vprev * span; }
-    else if (xa == 2) { Gs2 += vprev; As2 += vprev * span; }
-    const float Gv[3] = {Gs0, Gs1, Gs2};
-    const float Av[3] = {As0, As1, As2};
-    float d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = static_cast<float>(g[a]) * vd.delta[a];
-    const float L = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    const float FoL = acc / L;
-    const float am = static_cast<float>(amin);
-    float gt[3], gp[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (d[a] != 0.f) {
-        const float rd = L / d[a];
-        const float Aabs = fmaf(am, Gv[a], Av[a]);  // sum w * alpha (absolute alpha)
-        gt[a] = -Gv[a] * rd;                        // dE/dt_a = dE/ds_a + dE/dp_a
-        gp[a] = d[a] * FoL - Aabs * rd;             // dE/dp_a
-      } else {
-        gt[a] = 0.f;
-        gp[a] = 0.f;
-      }
+// Walk with the pose-Jacobian bookkeeping (Sec. 2.4).  Crossing k with weight
+// w_k = V_before - V_after adds to per-axis sums G_a = sum w, A_a = sum w alpha
+// (alpha from the entry).  Only the two axes with fewer crossings are summed;
+// the third follows from sum_k w_k = 0 and sum_k w_k alpha_k = F over all
+// crossings, entry and exit included (end points clamped to alpha = 0 or 1
+// belong to no axis and are kept in Gc, Ac).  When two crossings fall within
+// FP32 resolution of each other, their order -- which decides the voxel
+// between them and hence the weights -- is taken from FP64 alphas.
+struct JacSums {
+  float F, G[3], A[3], Gc, Ac;
+  int dom;
+};
+
+// Per-thread data the Jacobian walk needs only on its rare tie path, kept in
+// shared memory so that it does not occupy registers during the walk.
+struct TieScratch {
+  double fd[6][kThreads];  // FP64 first[3], delta[3] of each thread's ray
+  int cnt[3][kThreads];    // plane crossings per axis
+};
+
+template <bool kWant>
+struct TieSlot {
+  static __device__ __forceinline__ TieScratch* get() { return nullptr; }
+};
+template <>
+struct TieSlot<true> {
+  static __device__ __forceinline__ TieScratch* get() {
+    __shared__ TieScratch t;
+    return &t;
+  }
+};
+
+template <int DT>
+__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, TieScratch* tie,
+                                              JacSums& out) {
+  constexpr float kTieEps = 4.0e-7f;  // > twice the FP32 error of a crossing alpha (alpha <= 1)
+  const int t = threadIdx.x;
+  int dom = 0;
+  if (r.cnt[1] > r.cnt[dom]) dom = 1;
+  if (r.cnt[2] > r.cnt[dom]) dom = 2;
+  const int s0 = dom == 0 ? 1 : 0;  // the two summed axes
+  const int s1 = dom == 2 ? 1 : 2;
+  // slot per axis: 0 -> s0, 1 -> s1, 2 -> dom (not summed)
+  const int slx = s0 == 0 ? 0 : (s1 == 0 ? 1 : 2);
+  const int sly = s0 == 1 ? 0 : (s1 == 1 ? 1 : 2);
+  const int slz = s0 == 2 ? 0 : (s1 == 2 ? 1 : 2);
+  float ax = r.first[0], ay = r.first[1], az = r.first[2];
+  float kx = 0.f, ky = 0.f, kz = 0.f;
+  int off = r.off;
+  float v = Voxel<DT>::load(vd.data, off);
+  float acc = 0.f, ac = 0.f, vprev = 0.f;
+  float G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
+  int ps = r.ea == s0 ? 0 : (r.ea == s1 ? 1 : 2);  // slot of the crossing starting the current segment
+  if (r.ea < 0) Gc = -v;                           // entry clamped at alpha 0: weight -V_first
+  for (int m = 1; m < r.nseg; ++m) {
+    {  // the crossing that started the current segment (its voxel is known by now)
+      const float wgt = vprev - v;
+      if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, ac, A0); }
+      if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, ac, A1); }
     }
-    const float fw = static_cast<float>(w), fh = static_cast<float>(h);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float acc_j = 0.f;
+    const float mxy = fminf(ax, ay), Mxy = fmaxf(ax, ay);
+    const float an = fminf(mxy, az);
+    const float second = fmaxf(mxy, fminf(Mxy, az));
+    bool bx = ax == an;
+    bool by = !bx && ay == an;
+    if (second - an < kTieEps) {
+      // near-coincident crossings: order them with FP64 alphas (rare)
+      const float kk[3] = {kx, ky, kz};
+      double best = 1e300;
+      int sel = 2;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float Dja = fmaf(fh, pg.Hv[j][a], fmaf(fw, pg.Wv[j][a], pg.Q[j][a]));
-        acc_j = fmaf(gt[a], pg.S[j][a], acc_j);
-        acc_j = fmaf(gp[a], Dja, acc_j);
+        if (kk[a] < static_cast<float>(tie->cnt[a][t])) {
+          const double al = fma(static_cast<double>(kk[a]), tie->fd[3 + a][t], tie->fd[a][t]);
+          if (al < best) { best = al; sel = a; }
+        }
       }
-      res.J[j] = acc_j * vd.out_scale;
+      bx = sel == 0;
+      by = sel == 1;
     }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) res.J[3 + a] = gt[a] * vd.out_scale;
+    const bool bz = !bx && !by;
+    const float a_new = bx ? ax : (by ? ay : az);
+    off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
+    if (bx) kx += 1.f;
+    if (by) ky += 1.f;
+    if (bz) kz += 1.f;
+    ax = fmaf(kx, r.delta[0], r.first[0]);
+    ay = fmaf(ky, r.delta[1], r.first[1]);
+    az = fmaf(kz, r.delta[2], r.first[2]);
+    const float vn = Voxel<DT>::load(vd.data, off);
+    acc = fmaf(a_new - ac, v, acc);
+    ac = a_new;
+    ps = bx ? slx : (by ? sly : slz);
+    vprev = v;
+    v = vn;
   }
+  {
+    const float wgt = vprev - v;
+    if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, ac, A0); }
+    if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, ac, A1); }
+  }
+  acc = fmaf(r.span - ac, v, acc);
+  // exit crossing: weight V_last - 0 at alpha = span
+  float Ac = 0.f;
+  if (r.xa < 0) { Gc += v; Ac = v * r.span; }
+  else if (r.xa == s0) { G0 += v; A0 = fmaf(v, r.span, A0); }
+  else if (r.xa == s1) { G1 += v; A1 = fmaf(v, r.span, A1); }
+  out.F = acc;
+  out.dom = dom;
+  out.G[s0] = G0; out.A[s0] = A0;
+  out.G[s1] = G1; out.A[s1] = A1;
+  out.G[dom] = -(G0 + G1 + Gc);  // sum of all crossing weights is 0
+  out.A[dom] = 0.f;              // unused: the dominant axis is handled through R
+  out.Gc = Gc;
+  out.Ac = Ac;
+}
+
+// dE/d eta for one ray from the crossing sums (Sec. 2.4 with the voxel lookup
+// held fixed).  With d = p - s, L = |d|, absolute alphas A_abs = A + amin G:
+//   dE/dt_a = dE/ds_a + dE/dp_a = -L G_a / d_a
+//   dE/dp_a = d_a F / L - L A_abs_a / d_a
+// and for the dominant axis the second line is rearranged with
+// A_abs = F - R (R = the other axes' and the clamped points' A_abs) into
+//   dE/dp_a = (L R - F (L^2 - d_a^2) / L) / d_a,
+// which has no cancellation for rays nearly along that axis.
+//   dE/d eta_j = dE/dt . (dR_j s_c) + dE/dp . (dR_j (p_c - s_c)).
+__device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& s, const PoseGeom& pg, int h, int w,
+                                              float scale, float J[6]) {
+  const float L2 = r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2];
+  const float L = sqrtf(L2);
+  const float F = s.F;
+  const float am = static_cast<float>(r.amin);
+  float R = fmaf(am, s.Gc, s.Ac);
+  float gt[3], gp[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a != s.dom) R += fmaf(am, s.G[a], s.A[a]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (r.d[a] != 0.f) {
+      const float Ld = L / r.d[a];
+      gt[a] = -s.G[a] * Ld;
+      if (a == s.dom) {
+        float D = 0.f;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          if (b != a) D = fmaf(r.d[b], r.d[b], D);
+        gp[a] = (L * R - F * D / L) / r.d[a];
+      } else {
+        gp[a] = r.d[a] * F / L - fmaf(am, s.G[a], s.A[a]) * Ld;
+      }
+    } else {
+      gt[a] = 0.f;
+      gp[a] = 0.f;
+    }
+  }
+  const float fw = static_cast<float>(w), fh = static_cast<float>(h);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float Dja = fmaf(fh, pg.Hv[j][a], fmaf(fw, pg.Wv[j][a], pg.Q[j][a]));
+      acc = fmaf(gt[a], pg.S[j][a], acc);
+      acc = fmaf(gp[a], Dja, acc);
+    }
+    J[j] = acc * scale;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) J[3 + a] = gt[a] * scale;
+}
+
+// Back-projection walk: grad_V[voxel] += g L (a_{m+1} - a_m), the transpose of
+// the forward map V -> E; into an unpadded (nz, ny, nx) FP32 volume.
+__device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RaySetup& r, float gL,
+                                                 float* __restrict__ gvol) {
+  float ax = r.first[0], ay = r.first[1], az = r.first[2];
+  float kx = 0.f, ky = 0.f, kz = 0.f;
+  const int lx = r.step[0] > 0 ? 1 : -1;
+  const int ly = r.step[1] > 0 ? vd.n[0] : -vd.n[0];
+  const int lz = r.step[2] > 0 ? vd.n[0] * vd.n[1] : -(vd.n[0] * vd.n[1]);
+  const unsigned int nvox = static_cast<unsigned int>(vd.n[0] * vd.n[1] * vd.n[2]);
+  int lin = r.ient[0] + vd.n[0] * (r.ient[1] + vd.n[1] * r.ient[2]);
+  float ac = 0.f;
+  for (int m = 1; m < r.nseg; ++m) {
+    const float an = fminf(fminf(ax, ay), az);
+    if (static_cast<unsigned int>(lin) < nvox) atomicAdd(gvol + lin, gL * (an - ac));
+    ac = an;
+    if (ax == an) {
+      lin += lx; kx += 1.f; ax = fmaf(kx, r.delta[0], r.first[0]);
+    } else if (ay == an) {
+      lin += ly; ky += 1.f; ay = fmaf(ky, r.delta[1], r.first[1]);
+    } else {
+      lin += lz; kz += 1.f; az = fmaf(kz, r.delta[2], r.first[2]);
+    }
+  }
+  if (static_cast<unsigned int>(lin) < nvox) atomicAdd(gvol + lin, gL * (r.span - ac));
+}
+
+template <int MODE, int DT>
+__device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gscale,
+                                          float* __restrict__ gvol, TieScratch* tie, RayResult& res) {
+  res.F = 0.f;
+  res.nseg = 0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) res.J[k] = 0.f;
+  RaySetup r;
+  constexpr bool kJac = (MODE == kFwdJac || MODE == kPoseGrad);
+  double tieD[6];
+  const int rs = ray_setup(vd, pg, h, w, r, kJac ? tieD : nullptr);
+  if (rs < 0) {  // non-finite geometry (e.g. a NaN pose): NaN out, no walk
+    res.F = __int_as_float(0x7fffffff);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) res.J[k] = res.F;
+    return;
+  }
+  if (rs == 0) return;
+  res.nseg = r.nseg;
+  if (MODE == kCount) return;
+  if (kJac) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) tie->fd[a][threadIdx.x] = tieD[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tie->cnt[a][threadIdx.x] = r.cnt[a];
+  }
+  const float L = sqrtf(r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2]);
   if (MODE == kFwd) {
-    float d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = static_cast<float>(g[a]) * vd.delta[a];
-    res.F = acc * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * vd.out_scale;  // E
-  } else if (MODE == kFwdJac || MODE == kPoseGrad) {
-    float d[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = static_cast<float>(g[a]) * vd.delta[a];
-    res.F = acc * sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * vd.out_scale;
+    res.F = walk_forward<DT>(vd, r) * L * vd.out_scale;
+  } else if (kJac) {
+    JacSums s;
+    walk_jacobian<DT>(vd, r, tie, s);
+    res.F = s.F * L * vd.out_scale;
+    pose_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
+  } else if (MODE == kBackproject) {
+    walk_backproject(vd, r, gscale * L, gvol);
   }
 }
 
 template <int MODE, int DT>
-__global__ void __launch_bounds__(kThreads) siddon_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs,
+__global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGrad) ? 4 : 6) siddon_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs,
                                                           float* __restrict__ out, float* __restrict__ jac,
                                                           const float* __restrict__ gin,
                                                           float* __restrict__ partials, float* __restrict__ gvol) {
   __shared__ PoseGeom spg;
   __shared__ float red[kThreads / 32][6];
+  TieScratch* tie_sm = TieSlot<MODE == kFwdJac || MODE == kPoseGrad>::get();
   const int b = blockIdx.z;
   {
     const unsigned int* src = reinterpret_cast<const unsigned int*>(pgs + b);
@@ -396,7 +574,7 @@ __global__ void __launch_bounds__(kThreads) siddon_kernel(VolumeDev vd, DetDev d
   float gsc = 0.f;
   if (valid && (MODE == kPoseGrad || MODE == kBackproject)) gsc = gin[b * npix + pix];
   if (valid && !(MODE == kBackproject && gsc == 0.f)) {
-    trace_ray<MODE, DT>(vd, spg, h, w, gsc, gvol, r);
+    trace_ray<MODE, DT>(vd, spg, h, w, gsc, gvol, tie_sm, r);
   } else {
     r.F = 0.f;
 #pragma unroll
