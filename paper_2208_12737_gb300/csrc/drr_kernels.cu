@@ -17,8 +17,6 @@
 namespace drr {
 namespace {
 
-constexpr float kNoCrossing = 4.0f;  // relative alpha never exceeds 1
-
 enum Mode : int { kFwd = 0, kFwdJac = 1, kPoseGrad = 2, kBackproject = 3, kCount = 4 };
 
 template <int DT>
@@ -186,26 +184,37 @@ __device__ __forceinline__ void block_sum6(float v[6], float (*sm)[6]) {
   }
 }
 
-// Per-ray state after the FP64 setup: everything the FP32 walk needs.
+// Per-ray state after the FP64 setup: everything the walk needs.
+//
+// Crossing parameters are fixed point: alpha measured from the entry is held
+// as a 32.32 number in units of span / 2^30 (span = alpha_max - alpha_min), so
+// the high word of every crossing inside the ray lies in [0, 2^30] and the
+// exit is exactly 2^30.  Each axis' crossings form the arithmetic sequence
+// first + k * delta (Eq. 3), advanced by exact 64-bit additions: ordering is
+// exact to 2^-62 of the span and segment lengths are exact integers, so the
+// FP32 arithmetic is confined to the accumulation of length x density.
 struct RaySetup {
-  int nseg;        // segments = plane crossings + 1 (0: the ray misses)
-  int off;         // element offset of the entry voxel (padded layout)
-  int ient[3];     // entry voxel index per axis
-  int cnt[3];      // plane crossings per axis between the entry and exit voxels
-  int step[3];     // signed element stride per axis
-  int ea, xa;      // axis of the entry / exit plane, -1 when clamped to alpha = 0 / 1
-  float first[3];  // alpha (from the entry) of each axis' first crossing; kNoCrossing if none
-  float delta[3];  // alpha between consecutive planes of each axis
-  float span;      // alpha_max - alpha_min
-  double amin;     // absolute alpha of the entry
-  float d[3];      // p - s in mm
+  int nseg;                  // segments = plane crossings + 1 (0: the ray misses)
+  int off;                   // element offset of the entry voxel (padded layout)
+  int ient[3];               // entry voxel index per axis
+  int cnt[3];                // plane crossings per axis between the entry and exit voxels
+  int step[3];               // signed element stride per axis
+  int ea, xa;                // axis of the entry / exit plane, -1 when clamped to alpha = 0 / 1
+  unsigned long long A0[3];  // first crossing per axis (32.32 fixed point)
+  unsigned long long D[3];   // fixed-point distance between consecutive planes
+  float unit;                // alpha per fixed-point unit: span / 2^30
+  double amin;               // absolute alpha of the entry
+  float d[3];                // p - s in mm
 };
 
+constexpr unsigned int kExitUnits = 1u << 30;                    // the exit, in fixed-point units
+constexpr unsigned long long kNoCrossing64 = 0xC000000000000000ull;  // beyond any crossing of the ray
+constexpr double kFixScale = 4611686018427387904.0;              // 2^62: fixed-point value of alpha = span
+
 // FP64 clip (Sec. 2.3, clamped to [0, 1]), entry/exit voxels and first
-// crossings.  tieD receives FP64 first[3], delta[3] for exact tie ordering.
-// Returns 1 for a hit, 0 when the ray misses, -1 for non-finite geometry.
-__device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg, int h, int w, RaySetup& r,
-                                         double* tieD) {
+// crossings.  Returns 1 for a hit, 0 when the ray misses, -1 for non-finite
+// geometry.
+__device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg, int h, int w, RaySetup& r) {
   double g[3];
   bool finite = true;
 #pragma unroll
@@ -235,6 +244,9 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
   r.ea = ea;
   r.xa = xa;
   r.amin = amin;
+  const double span = amax - amin;
+  const double to_fix = kFixScale / span;  // fixed-point units per unit of alpha
+  r.unit = static_cast<float>(span / static_cast<double>(kExitUnits));
   int total = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -243,10 +255,9 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
     if (g[a] == 0.0) {
       r.ient[a] = min(max(static_cast<int>(floor(pg.u0[a])), 0), n - 1);
       r.cnt[a] = 0;
-      r.first[a] = kNoCrossing;
-      r.delta[a] = 0.f;
+      r.A0[a] = kNoCrossing64;
+      r.D[a] = 0ull;
       r.step[a] = vd.stride[a];
-      if (tieD) { tieD[a] = 4.0; tieD[3 + a] = 0.0; }
       continue;
     }
     const bool up = g[a] > 0.0;
@@ -263,50 +274,50 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
     r.cnt[a] = max(up ? i1 - i0 : i0 - i1, 0);
     total += r.cnt[a];
     const double plane = static_cast<double>(up ? i0 + 1 : i0);
-    const double f64 = (plane - ue) * rg[a];
-    r.first[a] = r.cnt[a] > 0 ? static_cast<float>(f64) : kNoCrossing;
-    r.delta[a] = static_cast<float>(fabs(rg[a]));
+    // first crossing, clamped into [0, span] (rounding can put it a hair outside)
+    const double f = fmin(fmax((plane - ue) * rg[a], 0.0), span);
+    r.A0[a] = r.cnt[a] > 0 ? static_cast<unsigned long long>(f * to_fix) : kNoCrossing64;
+    // plane spacing, saturated so that one step past the last plane cannot wrap
+    const double dfix = fmin(fabs(rg[a]) * to_fix, 2.0 * kFixScale);
+    r.D[a] = static_cast<unsigned long long>(dfix);
     r.step[a] = up ? vd.stride[a] : -vd.stride[a];
-    if (tieD) { tieD[a] = f64; tieD[3 + a] = fabs(rg[a]); }
   }
-  r.span = static_cast<float>(amax - amin);
   r.nseg = total + 1;
   r.off = vd.origin + r.ient[0] * vd.stride[0] + r.ient[1] * vd.stride[1] + r.ient[2] * vd.stride[2];
   return 1;
 }
 
+__device__ __forceinline__ unsigned int hi32(unsigned long long x) { return static_cast<unsigned int>(x >> 32); }
+
 // Forward walk (Sec. 2.2 Siddon-Jacobs, Eq. 2): sum (a_{m+1} - a_m) V over the
-// ray.  Crossings are ordered by their FP32 alphas; two crossings closer than
-// FP32 resolution change E only by that resolution times the density step.
-// The next voxel is loaded one iteration ahead of its use.  An axis whose
-// planes are used up can be picked once more only within FP32 rounding of the
-// exit, and that step lands in the zero padding.
+// ray, in fixed-point units.  The next voxel is loaded one iteration ahead of
+// its use.  An axis whose planes are used up can be picked once more only when
+// its next plane coincides with the exit to within a fixed-point unit; that
+// step lands in the zero padding and the remaining lengths are zero.
 template <int DT>
 __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetup& r) {
-  float ax = r.first[0], ay = r.first[1], az = r.first[2];
-  float kx = 0.f, ky = 0.f, kz = 0.f;
+  unsigned long long Ax = r.A0[0], Ay = r.A0[1], Az = r.A0[2];
   int off = r.off;
   float v = Voxel<DT>::load(vd.data, off);
-  float acc = 0.f, ac = 0.f;
+  float acc = 0.f;
+  unsigned int ac = 0u;
   for (int m = 1; m < r.nseg; ++m) {
-    // branch-free step of the axis with the nearest crossing
-    const float an = fminf(fminf(ax, ay), az);
-    const bool bx = ax == an;
-    const bool by = !bx && ay == an;
+    const unsigned int hx = hi32(Ax), hy = hi32(Ay), hz = hi32(Az);
+    const unsigned int an = min(min(hx, hy), hz);
+    const bool bx = hx == an;
+    const bool by = !bx && hy == an;
     const bool bz = !bx && !by;
     off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
-    if (bx) kx += 1.f;
-    if (by) ky += 1.f;
-    if (bz) kz += 1.f;
-    ax = fmaf(kx, r.delta[0], r.first[0]);
-    ay = fmaf(ky, r.delta[1], r.first[1]);
-    az = fmaf(kz, r.delta[2], r.first[2]);
+    if (bx) Ax += r.D[0];
+    if (by) Ay += r.D[1];
+    if (bz) Az += r.D[2];
     const float vn = Voxel<DT>::load(vd.data, off);
-    acc = fmaf(an - ac, v, acc);
+    acc = fmaf(static_cast<float>(static_cast<int>(an - ac)), v, acc);
     ac = an;
     v = vn;
   }
-  return fmaf(r.span - ac, v, acc);
+  acc = fmaf(static_cast<float>(static_cast<int>(kExitUnits - ac)), v, acc);
+  return acc * r.unit;
 }
 
 // Walk with the pose-Jacobian bookkeeping (Sec. 2.4).  Crossing k with weight
@@ -314,38 +325,16 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
 // (alpha from the entry).  Only the two axes with fewer crossings are summed;
 // the third follows from sum_k w_k = 0 and sum_k w_k alpha_k = F over all
 // crossings, entry and exit included (end points clamped to alpha = 0 or 1
-// belong to no axis and are kept in Gc, Ac).  When two crossings fall within
-// FP32 resolution of each other, their order -- which decides the voxel
-// between them and hence the weights -- is taken from FP64 alphas.
+// belong to no axis and are kept in Gc, Ac).  Crossings whose high words tie
+// are ordered by their full 64-bit values, which decides the voxel between
+// them and hence the weights.
 struct JacSums {
   float F, G[3], A[3], Gc, Ac;
   int dom;
 };
 
-// Per-thread data the Jacobian walk needs only on its rare tie path, kept in
-// shared memory so that it does not occupy registers during the walk.
-struct TieScratch {
-  double fd[6][kThreads];  // FP64 first[3], delta[3] of each thread's ray
-  int cnt[3][kThreads];    // plane crossings per axis
-};
-
-template <bool kWant>
-struct TieSlot {
-  static __device__ __forceinline__ TieScratch* get() { return nullptr; }
-};
-template <>
-struct TieSlot<true> {
-  static __device__ __forceinline__ TieScratch* get() {
-    __shared__ TieScratch t;
-    return &t;
-  }
-};
-
 template <int DT>
-__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, TieScratch* tie,
-                                              JacSums& out) {
-  constexpr float kTieEps = 4.0e-7f;  // > twice the FP32 error of a crossing alpha (alpha <= 1)
-  const int t = threadIdx.x;
+__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, JacSums& out) {
   int dom = 0;
   if (r.cnt[1] > r.cnt[dom]) dom = 1;
   if (r.cnt[2] > r.cnt[dom]) dom = 2;
@@ -355,75 +344,66 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
   const int slx = s0 == 0 ? 0 : (s1 == 0 ? 1 : 2);
   const int sly = s0 == 1 ? 0 : (s1 == 1 ? 1 : 2);
   const int slz = s0 == 2 ? 0 : (s1 == 2 ? 1 : 2);
-  float ax = r.first[0], ay = r.first[1], az = r.first[2];
-  float kx = 0.f, ky = 0.f, kz = 0.f;
+  unsigned long long Ax = r.A0[0], Ay = r.A0[1], Az = r.A0[2];
   int off = r.off;
   float v = Voxel<DT>::load(vd.data, off);
-  float acc = 0.f, ac = 0.f, vprev = 0.f;
+  float acc = 0.f, vprev = 0.f, acf = 0.f;
+  unsigned int ac = 0u;
   float G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
   int ps = r.ea == s0 ? 0 : (r.ea == s1 ? 1 : 2);  // slot of the crossing starting the current segment
   if (r.ea < 0) Gc = -v;                           // entry clamped at alpha 0: weight -V_first
   for (int m = 1; m < r.nseg; ++m) {
     {  // the crossing that started the current segment (its voxel is known by now)
       const float wgt = vprev - v;
-      if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, ac, A0); }
-      if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, ac, A1); }
+      if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, acf, A0); }
+      if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, acf, A1); }
     }
-    const float mxy = fminf(ax, ay), Mxy = fmaxf(ax, ay);
-    const float an = fminf(mxy, az);
-    const float second = fmaxf(mxy, fminf(Mxy, az));
-    bool bx = ax == an;
-    bool by = !bx && ay == an;
-    if (second - an < kTieEps) {
-      // near-coincident crossings: order them with FP64 alphas (rare)
-      const float kk[3] = {kx, ky, kz};
-      double best = 1e300;
-      int sel = 2;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (kk[a] < static_cast<float>(tie->cnt[a][t])) {
-          const double al = fma(static_cast<double>(kk[a]), tie->fd[3 + a][t], tie->fd[a][t]);
-          if (al < best) { best = al; sel = a; }
-        }
-      }
-      bx = sel == 0;
-      by = sel == 1;
+    const unsigned int hx = hi32(Ax), hy = hi32(Ay), hz = hi32(Az);
+    const unsigned int mxy = min(hx, hy), Mxy = max(hx, hy);
+    const unsigned int an = min(mxy, hz);
+    const unsigned int second = max(mxy, min(Mxy, hz));
+    bool bx = hx == an;
+    bool by = !bx && hy == an;
+    if (second == an) {  // two crossings in one unit: compare the full values (rare)
+      const unsigned long long best = min(min(Ax, Ay), Az);
+      bx = Ax == best;
+      by = !bx && Ay == best;
     }
     const bool bz = !bx && !by;
-    const float a_new = bx ? ax : (by ? ay : az);
     off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
-    if (bx) kx += 1.f;
-    if (by) ky += 1.f;
-    if (bz) kz += 1.f;
-    ax = fmaf(kx, r.delta[0], r.first[0]);
-    ay = fmaf(ky, r.delta[1], r.first[1]);
-    az = fmaf(kz, r.delta[2], r.first[2]);
+    if (bx) Ax += r.D[0];
+    if (by) Ay += r.D[1];
+    if (bz) Az += r.D[2];
     const float vn = Voxel<DT>::load(vd.data, off);
-    acc = fmaf(a_new - ac, v, acc);
-    ac = a_new;
+    acc = fmaf(static_cast<float>(static_cast<int>(an - ac)), v, acc);
+    ac = an;
+    acf = static_cast<float>(static_cast<int>(an));
     ps = bx ? slx : (by ? sly : slz);
     vprev = v;
     v = vn;
   }
   {
     const float wgt = vprev - v;
-    if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, ac, A0); }
-    if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, ac, A1); }
+    if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, acf, A0); }
+    if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, acf, A1); }
   }
-  acc = fmaf(r.span - ac, v, acc);
-  // exit crossing: weight V_last - 0 at alpha = span
+  acc = fmaf(static_cast<float>(static_cast<int>(kExitUnits - ac)), v, acc);
+  // exit crossing: weight V_last - 0 at the exit
+  const float ex = static_cast<float>(kExitUnits);
   float Ac = 0.f;
-  if (r.xa < 0) { Gc += v; Ac = v * r.span; }
-  else if (r.xa == s0) { G0 += v; A0 = fmaf(v, r.span, A0); }
-  else if (r.xa == s1) { G1 += v; A1 = fmaf(v, r.span, A1); }
-  out.F = acc;
+  if (r.xa < 0) { Gc += v; Ac = v * ex; }
+  else if (r.xa == s0) { G0 += v; A0 = fmaf(v, ex, A0); }
+  else if (r.xa == s1) { G1 += v; A1 = fmaf(v, ex, A1); }
+  // back to alpha units
+  const float u = r.unit;
+  out.F = acc * u;
   out.dom = dom;
-  out.G[s0] = G0; out.A[s0] = A0;
-  out.G[s1] = G1; out.A[s1] = A1;
+  out.G[s0] = G0; out.A[s0] = A0 * u;
+  out.G[s1] = G1; out.A[s1] = A1 * u;
   out.G[dom] = -(G0 + G1 + Gc);  // sum of all crossing weights is 0
   out.A[dom] = 0.f;              // unused: the dominant axis is handled through R
   out.Gc = Gc;
-  out.Ac = Ac;
+  out.Ac = Ac * u;
 }
 
 // dE/d eta for one ray from the crossing sums (Sec. 2.4 with the voxel lookup
@@ -485,40 +465,41 @@ __device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& 
 // the forward map V -> E; into an unpadded (nz, ny, nx) FP32 volume.
 __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RaySetup& r, float gL,
                                                  float* __restrict__ gvol) {
-  float ax = r.first[0], ay = r.first[1], az = r.first[2];
-  float kx = 0.f, ky = 0.f, kz = 0.f;
+  unsigned long long Ax = r.A0[0], Ay = r.A0[1], Az = r.A0[2];
   const int lx = r.step[0] > 0 ? 1 : -1;
   const int ly = r.step[1] > 0 ? vd.n[0] : -vd.n[0];
   const int lz = r.step[2] > 0 ? vd.n[0] * vd.n[1] : -(vd.n[0] * vd.n[1]);
   const unsigned int nvox = static_cast<unsigned int>(vd.n[0] * vd.n[1] * vd.n[2]);
   int lin = r.ient[0] + vd.n[0] * (r.ient[1] + vd.n[1] * r.ient[2]);
-  float ac = 0.f;
+  const float s = gL * r.unit;
+  unsigned int ac = 0u;
   for (int m = 1; m < r.nseg; ++m) {
-    const float an = fminf(fminf(ax, ay), az);
-    if (static_cast<unsigned int>(lin) < nvox) atomicAdd(gvol + lin, gL * (an - ac));
+    const unsigned int hx = hi32(Ax), hy = hi32(Ay), hz = hi32(Az);
+    const unsigned int an = min(min(hx, hy), hz);
+    if (static_cast<unsigned int>(lin) < nvox)
+      atomicAdd(gvol + lin, s * static_cast<float>(static_cast<int>(an - ac)));
     ac = an;
-    if (ax == an) {
-      lin += lx; kx += 1.f; ax = fmaf(kx, r.delta[0], r.first[0]);
-    } else if (ay == an) {
-      lin += ly; ky += 1.f; ay = fmaf(ky, r.delta[1], r.first[1]);
-    } else {
-      lin += lz; kz += 1.f; az = fmaf(kz, r.delta[2], r.first[2]);
-    }
+    const bool bx = hx == an;
+    const bool by = !bx && hy == an;
+    const bool bz = !bx && !by;
+    lin += bx ? lx : (by ? ly : lz);
+    if (bx) Ax += r.D[0];
+    if (by) Ay += r.D[1];
+    if (bz) Az += r.D[2];
   }
-  if (static_cast<unsigned int>(lin) < nvox) atomicAdd(gvol + lin, gL * (r.span - ac));
+  if (static_cast<unsigned int>(lin) < nvox)
+    atomicAdd(gvol + lin, s * static_cast<float>(static_cast<int>(kExitUnits - ac)));
 }
 
 template <int MODE, int DT>
 __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gscale,
-                                          float* __restrict__ gvol, TieScratch* tie, RayResult& res) {
+                                          float* __restrict__ gvol, RayResult& res) {
   res.F = 0.f;
   res.nseg = 0;
 #pragma unroll
   for (int k = 0; k < 6; ++k) res.J[k] = 0.f;
   RaySetup r;
-  constexpr bool kJac = (MODE == kFwdJac || MODE == kPoseGrad);
-  double tieD[6];
-  const int rs = ray_setup(vd, pg, h, w, r, kJac ? tieD : nullptr);
+  const int rs = ray_setup(vd, pg, h, w, r);
   if (rs < 0) {  // non-finite geometry (e.g. a NaN pose): NaN out, no walk
     res.F = __int_as_float(0x7fffffff);
 #pragma unroll
@@ -528,18 +509,12 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
   if (rs == 0) return;
   res.nseg = r.nseg;
   if (MODE == kCount) return;
-  if (kJac) {
-#pragma unroll
-    for (int a = 0; a < 6; ++a) tie->fd[a][threadIdx.x] = tieD[a];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) tie->cnt[a][threadIdx.x] = r.cnt[a];
-  }
   const float L = sqrtf(r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2]);
   if (MODE == kFwd) {
     res.F = walk_forward<DT>(vd, r) * L * vd.out_scale;
-  } else if (kJac) {
+  } else if (MODE == kFwdJac || MODE == kPoseGrad) {
     JacSums s;
-    walk_jacobian<DT>(vd, r, tie, s);
+    walk_jacobian<DT>(vd, r, s);
     res.F = s.F * L * vd.out_scale;
     pose_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
   } else if (MODE == kBackproject) {
@@ -554,7 +529,6 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
                                                           float* __restrict__ partials, float* __restrict__ gvol) {
   __shared__ PoseGeom spg;
   __shared__ float red[kThreads / 32][6];
-  TieScratch* tie_sm = TieSlot<MODE == kFwdJac || MODE == kPoseGrad>::get();
   const int b = blockIdx.z;
   {
     const unsigned int* src = reinterpret_cast<const unsigned int*>(pgs + b);
@@ -574,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
   float gsc = 0.f;
   if (valid && (MODE == kPoseGrad || MODE == kBackproject)) gsc = gin[b * npix + pix];
   if (valid && !(MODE == kBackproject && gsc == 0.f)) {
-    trace_ray<MODE, DT>(vd, spg, h, w, gsc, gvol, tie_sm, r);
+    trace_ray<MODE, DT>(vd, spg, h, w, gsc, gvol, r);
   } else {
     r.F = 0.f;
 #pragma unroll
