@@ -148,6 +148,80 @@ drr_status drr_ray_setup(const drr_detector* det, const float* poses_dev, int32_
 drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
                               int32_t* segments_out_dev, void* cuda_stream);
 
+/* ---- serving: continuous batching of render / render+gradient requests ---- */
+/* No counterpart in the paper (whose method is a library call); this is the
+ * request loop of the serving workload.  A host thread forms "ticks": it admits
+ * queued requests while slots and the explicit memory budgets allow, uploads
+ * their poses (and upstream gradients), and runs one pose-setup, one persistent
+ * ray-walk and one gradient-finalise launch that cover the rays of every
+ * admitted request, mixed volumes, dtypes and detectors included (optionally
+ * replayed from a captured CUDA graph).  Two ticks can be in flight: requests
+ * arriving while one tick runs are admitted into the next.  Results of a request
+ * are identical whether it ran alone or in a mix (the per-ray arithmetic and the
+ * gradient reduction order do not depend on the other requests). */
+
+typedef struct {
+  size_t device_budget_bytes; /* device memory reserved for request buffers; 0 -> 512 MiB */
+  size_t host_budget_bytes;   /* pinned host staging; 0 -> the device budget */
+  int32_t max_inflight;       /* requests admitted at once (slots); 0 -> 64 */
+  int32_t max_tick_poses;     /* poses packed into one tick; 0 -> 4096 (also the largest B accepted) */
+  int32_t use_cuda_graph;     /* nonzero: replay the tick's three launches from a captured graph */
+  int32_t device;             /* CUDA device ordinal; -1 -> the current device */
+} drr_server_config;
+
+typedef struct {
+  drr_volume volume;        /* must stay alive until the request completes (destroy returns BUSY) */
+  drr_detector detector;
+  int32_t B;                /* poses, 1 .. max_tick_poses */
+  const float* poses;       /* host [B][6] */
+  const float* grad_drr;    /* host [B][H][W] dL/dE for a render+gradient request, or NULL */
+  float* drr_out;           /* host [B][H][W], written before drr_server_wait returns DRR_OK */
+  float* grad_pose_out;     /* host [B][6], required iff grad_drr != NULL */
+} drr_request;
+/* All host buffers of a request are caller-owned and must stay valid until
+ * drr_server_wait has returned for its ticket. */
+
+typedef struct {
+  int32_t status;    /* drr_status of the request */
+  double queue_ms;   /* submit -> admitted into a tick */
+  double latency_ms; /* submit -> results written to the caller's buffers */
+  int64_t tick;      /* tick that ran it (-1 if it never ran) */
+} drr_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, cancelled, ticks;
+  int32_t pending, inflight;
+  size_t device_in_use, device_budget;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed requests */
+  double gpu_busy_ms;                     /* summed device time of the ticks */
+} drr_server_stats;
+
+/* Start a server (allocates both budgets up front; DRR_ERR_OOM if it cannot). */
+drr_status drr_server_create(const drr_server_config* cfg, drr_server* out);
+/* Queue a request; returns a ticket.  Validation errors are DRR_ERR_INVALID; a
+ * request that can never fit the budgets is DRR_ERR_OOM. */
+drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a ticket.  Returns the request's
+ * status (DRR_OK, DRR_ERR_CANCELLED, ...) and releases the ticket, or
+ * DRR_ERR_TIMEOUT (ticket kept), or DRR_ERR_NOT_FOUND for an unknown ticket. */
+drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, drr_result* res);
+/* Cancel a request that has not been admitted yet; DRR_ERR_BUSY once it has. */
+drr_status drr_server_cancel(drr_server s, uint64_t ticket);
+drr_status drr_server_get_stats(drr_server s, drr_server_stats* out);
+/* Finish in-flight ticks, cancel queued requests and free everything. */
+drr_status drr_server_destroy(drr_server s);
+
+/* ---- host-side offset arena (the servers' admission allocator) ----------- */
+/* A first-fit allocator over [0, capacity) with alignment and coalescing; it
+ * makes no CUDA calls.  Exposed so its policy can be tested on its own. */
+typedef struct drr_arena_s* drr_arena;
+drr_status drr_arena_create(size_t capacity, size_t align, drr_arena* out);
+drr_status drr_arena_alloc(drr_arena a, size_t bytes, size_t* offset); /* DRR_ERR_OOM if no run fits */
+drr_status drr_arena_free(drr_arena a, size_t offset);                 /* DRR_ERR_NOT_FOUND if unknown */
+size_t drr_arena_in_use(drr_arena a);
+size_t drr_arena_largest_free(drr_arena a);
+drr_status drr_arena_destroy(drr_arena a);
+
 /* ---- profiling (no counterpart in the paper) ------------------------------ */
 
 /* While enabled, every kernel launch is bracketed by CUDA events recorded on

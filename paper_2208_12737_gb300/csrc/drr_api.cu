@@ -14,19 +14,13 @@
 #include "drr.h"
 #include "drr_internal.cuh"
 
-struct drr_volume_s {
-  void* storage = nullptr;
-  size_t bytes = 0;
-  int device = 0;
-  drr::VolumeDev vd{};
-  std::atomic<int> refs{0};  // held by servers
-};
-
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
-drr_status fail(drr_status st, const char* fmt, ...) {
+namespace drr {
+
+drr_status set_error(drr_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -36,15 +30,28 @@ drr_status fail(drr_status st, const char* fmt, ...) {
   return st;
 }
 
-drr_status cuda_fail(cudaError_t e, const char* what) {
-  return fail(e == cudaErrorMemoryAllocation ? DRR_ERR_OOM : DRR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+drr_status cuda_error(cudaError_t e, const char* what) {
+  return set_error(e == cudaErrorMemoryAllocation ? DRR_ERR_OOM : DRR_ERR_CUDA, "%s: %s", what,
+                   cudaGetErrorString(e));
 }
+
+}  // namespace drr
+
+namespace {
+
+using drr::check_detector;
+using drr::check_geometry;
+using drr::configure_pool;
 
 #define DRR_CUDA(call, what)                  \
   do {                                        \
     cudaError_t e_ = (call);                  \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    if (e_ != cudaSuccess) return drr::cuda_error(e_, what); \
   } while (0)
+
+}  // namespace
+
+namespace drr {
 
 // Stream-ordered scratch comes from the device's default memory pool; keep
 // freed blocks cached in the pool instead of returning them to the driver.
@@ -61,13 +68,13 @@ void configure_pool(int dev) {
 }
 
 drr_status check_detector(const drr_detector* det, drr::DetDev* out) {
-  if (!det) return fail(DRR_ERR_INVALID, "detector is NULL");
-  if (det->height <= 0 || det->width <= 0) return fail(DRR_ERR_INVALID, "detector size must be positive");
+  if (!det) return drr::set_error(DRR_ERR_INVALID, "detector is NULL");
+  if (det->height <= 0 || det->width <= 0) return drr::set_error(DRR_ERR_INVALID, "detector size must be positive");
   if (!(det->sdr_mm > 0.f) || !(det->delta_h_mm > 0.f) || !(det->delta_w_mm > 0.f) || !std::isfinite(det->sdr_mm) ||
       !std::isfinite(det->delta_h_mm) || !std::isfinite(det->delta_w_mm))
-    return fail(DRR_ERR_INVALID, "detector distances must be positive and finite");
+    return drr::set_error(DRR_ERR_INVALID, "detector distances must be positive and finite");
   if (static_cast<int64_t>(det->height) * det->width > (int64_t{1} << 30))
-    return fail(DRR_ERR_INVALID, "detector has too many pixels");
+    return drr::set_error(DRR_ERR_INVALID, "detector has too many pixels");
   out->H = det->height;
   out->W = det->width;
   out->sdr = det->sdr_mm;
@@ -83,12 +90,16 @@ drr_status check_geometry(const drr::VolumeDev& vd, const drr::DetDev& det) {
   double Lmax = std::sqrt(double(det.sdr) * det.sdr + hw * hw + hh * hh);
   double dmin = std::fmin(vd.delta[0], std::fmin(vd.delta[1], vd.delta[2]));
   if (Lmax / dmin >= double(1 << 20))
-    return fail(DRR_ERR_INVALID, "ray length / voxel spacing too large (%.3g >= 2^20)", Lmax / dmin);
+    return drr::set_error(DRR_ERR_INVALID, "ray length / voxel spacing too large (%.3g >= 2^20)", Lmax / dmin);
   return DRR_OK;
 }
 
+}  // namespace drr
+
+namespace {
+
 drr_status check_volume(drr_volume v) {
-  if (!v || !v->storage) return fail(DRR_ERR_INVALID, "volume handle is NULL or destroyed");
+  if (!v || !v->storage) return drr::set_error(DRR_ERR_INVALID, "volume handle is NULL or destroyed");
   return DRR_OK;
 }
 
@@ -160,6 +171,12 @@ struct LaunchScope {
   }
 };
 
+}  // namespace
+
+void drr::count_launches(int n) { g_launches.fetch_add(n); }
+
+namespace {
+
 drr_status setup_geometry(drr_volume v, const drr::DetDev& dd, const float* poses_dev, int32_t B, cudaStream_t st,
                           AsyncBuf<drr::PoseGeom>& pg) {
   DRR_CUDA(pg.alloc(size_t(B), st), "cudaMallocAsync(pose geometry)");
@@ -189,11 +206,11 @@ drr_status drr_profile_reset(void) {
 }
 
 drr_status drr_profile_read(const char* kernel, double* total_ms, int64_t* launches) {
-  if (!kernel || !total_ms || !launches) return fail(DRR_ERR_INVALID, "NULL argument");
+  if (!kernel || !total_ms || !launches) return drr::set_error(DRR_ERR_INVALID, "NULL argument");
   int k = -1;
   for (int i = 0; i < kNumProf; ++i)
     if (std::strcmp(kernel, kProfNames[i]) == 0) k = i;
-  if (k < 0) return fail(DRR_ERR_INVALID, "unknown kernel name '%s'", kernel);
+  if (k < 0) return drr::set_error(DRR_ERR_INVALID, "unknown kernel name '%s'", kernel);
   std::lock_guard<std::mutex> lk(g_prof_mu);
   double ms = 0.0;
   int64_t n = 0;
@@ -219,28 +236,28 @@ const char* drr_version(void) { return "libdrr 0.1 (sm_103a)"; }
 drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype src_dtype, int32_t nx, int32_t ny,
                              int32_t nz, float dx_mm, float dy_mm, float dz_mm, const drr_volume_options* opt,
                              void* cuda_stream, drr_volume* out) {
-  if (!out) return fail(DRR_ERR_INVALID, "out is NULL");
+  if (!out) return drr::set_error(DRR_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (!data) return fail(DRR_ERR_INVALID, "data is NULL");
+  if (!data) return drr::set_error(DRR_ERR_INVALID, "data is NULL");
   if (src_dtype != DRR_F32 && src_dtype != DRR_I16_HU)
-    return fail(DRR_ERR_INVALID, "src_dtype must be DRR_F32 or DRR_I16_HU");
-  if (nx <= 0 || ny <= 0 || nz <= 0) return fail(DRR_ERR_INVALID, "volume dims must be positive");
+    return drr::set_error(DRR_ERR_INVALID, "src_dtype must be DRR_F32 or DRR_I16_HU");
+  if (nx <= 0 || ny <= 0 || nz <= 0) return drr::set_error(DRR_ERR_INVALID, "volume dims must be positive");
   if (!(dx_mm > 0.f && dy_mm > 0.f && dz_mm > 0.f) || !std::isfinite(dx_mm) || !std::isfinite(dy_mm) ||
       !std::isfinite(dz_mm))
-    return fail(DRR_ERR_INVALID, "voxel spacing must be positive and finite");
+    return drr::set_error(DRR_ERR_INVALID, "voxel spacing must be positive and finite");
   const int64_t padded = int64_t(nx + 2) * (ny + 2) * (nz + 2);
-  if (padded >= (int64_t{1} << 31)) return fail(DRR_ERR_INVALID, "volume too large (padded voxels >= 2^31)");
+  if (padded >= (int64_t{1} << 31)) return drr::set_error(DRR_ERR_INVALID, "volume too large (padded voxels >= 2^31)");
   drr_dtype storage = DRR_F32;
   float mu_water = 0.02f;
   if (opt) {
     storage = opt->storage;
     if (opt->hu_mu_water != 0.f) mu_water = opt->hu_mu_water;
     if (opt->layout != 0 && opt->layout != 1)
-      return fail(DRR_ERR_INVALID, "layout %d not supported (0 or 1)", opt->layout);
+      return drr::set_error(DRR_ERR_INVALID, "layout %d not supported (0 or 1)", opt->layout);
   }
   if (storage != DRR_F32 && storage != DRR_BF16 && storage != DRR_F16)
-    return fail(DRR_ERR_INVALID, "storage dtype must be DRR_F32, DRR_BF16 or DRR_F16");
-  if (!(mu_water > 0.f) || !std::isfinite(mu_water)) return fail(DRR_ERR_INVALID, "hu_mu_water must be positive");
+    return drr::set_error(DRR_ERR_INVALID, "storage dtype must be DRR_F32, DRR_BF16 or DRR_F16");
+  if (!(mu_water > 0.f) || !std::isfinite(mu_water)) return drr::set_error(DRR_ERR_INVALID, "hu_mu_water must be positive");
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int dev = 0;
@@ -256,7 +273,7 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
     cudaError_t e = cudaMemcpyAsync(staged, data, src_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
       cudaFreeAsync(staged, st);
-      return cuda_fail(e, "cudaMemcpyAsync(volume upload)");
+      return drr::cuda_error(e, "cudaMemcpyAsync(volume upload)");
     }
     src = staged;
   }
@@ -296,7 +313,7 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
     if (e != cudaSuccess) {
       cleanup();
       delete v;
-      return cuda_fail(e, "volume max for FP16 scale");
+      return drr::cuda_error(e, "volume max for FP16 scale");
     }
     float mx;
     std::memcpy(&mx, &hbits, 4);
@@ -313,7 +330,7 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
   if (e != cudaSuccess) {
     cleanup();
     delete v;
-    return cuda_fail(e, "cudaMalloc(volume storage)");
+    return drr::cuda_error(e, "cudaMalloc(volume storage)");
   }
   vd.data = v->storage;
   e = drr::launch_ingest(src, src_dtype == DRR_I16_HU ? 3 : 0, mu_water, vd, v->storage, scale, st);
@@ -322,7 +339,7 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
   if (e != cudaSuccess) {
     cudaFree(v->storage);
     delete v;
-    return cuda_fail(e, "volume ingest");
+    return drr::cuda_error(e, "volume ingest");
   }
   *out = v;
   return DRR_OK;
@@ -330,7 +347,7 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
 
 drr_status drr_volume_destroy(drr_volume v) {
   if (!v) return DRR_OK;
-  if (v->refs.load() > 0) return fail(DRR_ERR_BUSY, "volume is still referenced by %d server(s)", v->refs.load());
+  if (v->refs.load() > 0) return drr::set_error(DRR_ERR_BUSY, "volume is still referenced by %d server(s)", v->refs.load());
   if (v->storage) {
     int cur = 0;
     cudaGetDevice(&cur);
@@ -359,8 +376,8 @@ drr_status drr_ray_setup(const drr_detector* det, const float* poses_dev, int32_
                          void* cuda_stream) {
   drr::DetDev dd;
   if (drr_status s = check_detector(det, &dd)) return s;
-  if (B <= 0) return fail(DRR_ERR_INVALID, "B must be positive");
-  if (!poses_dev || !rays_out_dev) return fail(DRR_ERR_INVALID, "NULL pointer");
+  if (B <= 0) return drr::set_error(DRR_ERR_INVALID, "B must be positive");
+  if (!poses_dev || !rays_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   LaunchScope ls(kPoseSetup, static_cast<cudaStream_t>(cuda_stream));
   DRR_CUDA(drr::launch_ray_setup(poses_dev, B, dd, rays_out_dev, static_cast<cudaStream_t>(cuda_stream)),
            "ray_setup launch");
@@ -373,9 +390,9 @@ drr_status drr_render(drr_volume v, const drr_detector* det, const float* poses_
   drr::DetDev dd;
   if (drr_status s = check_detector(det, &dd)) return s;
   if (drr_status s = check_geometry(v->vd, dd)) return s;
-  if (B <= 0) return fail(DRR_ERR_INVALID, "B must be positive");
-  if (B > 65535) return fail(DRR_ERR_INVALID, "B must be <= 65535");
-  if (!poses_dev || !drr_out_dev) return fail(DRR_ERR_INVALID, "NULL pointer");
+  if (B <= 0) return drr::set_error(DRR_ERR_INVALID, "B must be positive");
+  if (B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be <= 65535");
+  if (!poses_dev || !drr_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -392,11 +409,11 @@ drr_status drr_render_backward(drr_volume v, const drr_detector* det, const floa
   drr::DetDev dd;
   if (drr_status s = check_detector(det, &dd)) return s;
   if (drr_status s = check_geometry(v->vd, dd)) return s;
-  if (B <= 0) return fail(DRR_ERR_INVALID, "B must be positive");
-  if (B > 65535) return fail(DRR_ERR_INVALID, "B must be <= 65535");
-  if (!poses_dev || !grad_drr_dev) return fail(DRR_ERR_INVALID, "NULL pointer");
+  if (B <= 0) return drr::set_error(DRR_ERR_INVALID, "B must be positive");
+  if (B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be <= 65535");
+  if (!poses_dev || !grad_drr_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   if (!grad_pose_dev && !grad_volume_dev)
-    return fail(DRR_ERR_INVALID, "nothing to compute: grad_pose_dev and grad_volume_dev are both NULL");
+    return drr::set_error(DRR_ERR_INVALID, "nothing to compute: grad_pose_dev and grad_volume_dev are both NULL");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -429,8 +446,8 @@ drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float
   drr::DetDev dd;
   if (drr_status s = check_detector(det, &dd)) return s;
   if (drr_status s = check_geometry(v->vd, dd)) return s;
-  if (B <= 0 || B > 65535) return fail(DRR_ERR_INVALID, "B must be in [1, 65535]");
-  if (!poses_dev || !segments_out_dev) return fail(DRR_ERR_INVALID, "NULL pointer");
+  if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
+  if (!poses_dev || !segments_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -442,9 +459,9 @@ drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float
 
 drr_status drr_stream_check(void* cuda_stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
-  if (e != cudaSuccess) return cuda_fail(e, "stream");
+  if (e != cudaSuccess) return drr::cuda_error(e, "stream");
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "pending error");
+  if (e != cudaSuccess) return drr::cuda_error(e, "pending error");
   return DRR_OK;
 }
 

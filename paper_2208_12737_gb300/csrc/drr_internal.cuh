@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
+#include "drr.h"
+
 namespace drr {
 
 // Pixel tiling of the ray kernels: a 256-thread block covers 32 x 8 pixels,
@@ -51,6 +55,29 @@ struct DetDev {
   float sdr, dh, dw;
 };
 
+// One admitted request as the serving kernels see it (device-resident table).
+struct ServeRequest {
+  VolumeDev vd;
+  DetDev det;
+  const float* poses;  // [B][6]
+  const float* grad;   // [B][H][W] upstream gradient, or null for render-only requests
+  float* out;          // [B][H][W]
+  float* partials;     // [B][tiles per pose][6] (gradient requests)
+  float* grad_pose;    // [B][6] (gradient requests)
+  PoseGeom* geom;      // [B]
+  int B, tiles_x, tiles_y;
+  int tile_start;      // first tile of this request in the tick's global tile numbering
+  int pose_start;      // first pose of this request in the tick's global pose numbering
+  int pad_;
+};
+
+struct ServeHeader {
+  int nreq;
+  int total_tiles;
+  int total_poses;
+  int pad_;
+};
+
 // Launchers (drr_kernels.cu).  All enqueue on `stream` and return the
 // cudaGetLastError() of the launch.
 cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, const VolumeDev* vd, PoseGeom* out,
@@ -68,10 +95,34 @@ cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const 
                                   cudaStream_t stream);
 cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
                                const float* grad_drr, float* grad_vol, cudaStream_t stream);
+// Serving tick: pose setup over all poses of the tick, the persistent walk
+// over all tiles (tiles claimed through *counter, which must be zero), and the
+// fixed-order pose-gradient sums.  Grids are fixed so the three launches can be
+// captured once in a CUDA graph; the counts are read from the device header.
+int serve_walk_grid(int device);
+cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, int* counter, int max_poses,
+                              int walk_grid, cudaStream_t stream);
 // Volume ingest.
 cudaError_t launch_abs_max(const void* src, int src_dtype, int64_t count, float mu_water, unsigned int* out_bits,
                            cudaStream_t stream);
 cudaError_t launch_ingest(const void* src, int src_dtype, float mu_water, const VolumeDev& vd, void* dst,
                           float scale, cudaStream_t stream);
 
+// ---- host-side helpers shared by the C-ABI files (drr_api.cu) -------------
+drr_status set_error(drr_status st, const char* fmt, ...);
+drr_status cuda_error(cudaError_t e, const char* what);
+drr_status check_detector(const drr_detector* det, DetDev* out);
+drr_status check_geometry(const VolumeDev& vd, const DetDev& det);
+void configure_pool(int dev);
+void count_launches(int n);  // kernel launches issued outside LaunchScope (serving ticks)
+
 }  // namespace drr
+
+// A device-resident volume (drr_volume_create).
+struct drr_volume_s {
+  void* storage = nullptr;
+  size_t bytes = 0;
+  int device = 0;
+  drr::VolumeDev vd{};
+  std::atomic<int> refs{0};  // requests queued or running in servers
+};

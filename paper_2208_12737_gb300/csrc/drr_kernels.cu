@@ -100,13 +100,10 @@ __device__ void pose_frame(const float* pose, const DetDev& det, double s[3], do
   }
 }
 
-__global__ void pose_setup_kernel(const float* __restrict__ poses, int B, DetDev det, VolumeDev vd,
-                                  PoseGeom* __restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+// Per-pose geometry in the volume's voxel units plus the chain-rule terms.
+__device__ void compute_pose_geom(const float* pose, const DetDev& det, const VolumeDev& vd, PoseGeom& g) {
   double s[3], p00[3], ew[3], eh[3], sc[3], pc00[3], dR[27];
-  pose_frame(poses + 6 * b, det, s, p00, ew, eh, sc, pc00, dR);
-  PoseGeom g;
+  pose_frame(pose, det, s, p00, ew, eh, sc, pc00, dR);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double dl = static_cast<double>(vd.delta[a]);
@@ -132,6 +129,14 @@ __global__ void pose_setup_kernel(const float* __restrict__ poses, int B, DetDev
     apply3(dR + 9 * j, vh, t);
     for (int a = 0; a < 3; ++a) g.Hv[j][a] = static_cast<float>(t[a]);
   }
+}
+
+__global__ void pose_setup_kernel(const float* __restrict__ poses, int B, DetDev det, VolumeDev vd,
+                                  PoseGeom* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  PoseGeom g;
+  compute_pose_geom(poses + 6 * b, det, vd, g);
   out[b] = g;
 }
 
@@ -658,6 +663,131 @@ __global__ void ingest_kernel(const void* __restrict__ src, int src_dtype, float
   }
 }
 
+// ---------------------------------------------------------------------------
+// Serving tick kernels: one launch each covers every admitted request.
+// ---------------------------------------------------------------------------
+// Index of the request whose [start, next start) range holds `i` (starts ascending).
+__device__ __forceinline__ int find_request(const ServeRequest* reqs, int nreq, int i, bool by_tile) {
+  int lo = 0, hi = nreq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int st = by_tile ? reqs[mid].tile_start : reqs[mid].pose_start;
+    if (st <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void serve_setup_kernel(const ServeHeader* __restrict__ hdr, const ServeRequest* __restrict__ reqs) {
+  const int nreq = hdr->nreq, total = hdr->total_poses;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int r = find_request(reqs, nreq, i, false);
+    const int b = i - reqs[r].pose_start;
+    PoseGeom g;
+    compute_pose_geom(reqs[r].poses + 6 * b, reqs[r].det, reqs[r].vd, g);
+    reqs[r].geom[b] = g;
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void serve_trace(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gsc,
+                                            RayResult& r) {
+  switch (vd.dtype) {
+    case kF32: trace_ray<MODE, kF32>(vd, pg, h, w, gsc, nullptr, r); break;
+    case kBF16: trace_ray<MODE, kBF16>(vd, pg, h, w, gsc, nullptr, r); break;
+    default: trace_ray<MODE, kF16>(vd, pg, h, w, gsc, nullptr, r); break;
+  }
+}
+
+// Persistent walk: blocks claim 32x8-pixel tiles of any request until the
+// tick's tiles run out; render-only tiles run the forward walk, gradient
+// tiles the Jacobian walk with the block's sum of g . J written per tile.
+__global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHeader* __restrict__ hdr,
+                                                                 const ServeRequest* __restrict__ reqs,
+                                                                 int* __restrict__ counter) {
+  __shared__ PoseGeom spg;
+  __shared__ ServeRequest sr;
+  __shared__ float red[kThreads / 32][6];
+  __shared__ int s_tile;
+  const int nreq = hdr->nreq, total = hdr->total_tiles;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= total) break;
+    const int r = find_request(reqs, nreq, t, true);
+    {
+      const unsigned int* src = reinterpret_cast<const unsigned int*>(reqs + r);
+      unsigned int* dst = reinterpret_cast<unsigned int*>(&sr);
+      for (int i = threadIdx.x; i < static_cast<int>(sizeof(ServeRequest) / 4); i += kThreads) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int per_pose = sr.tiles_x * sr.tiles_y;
+    const int local = t - sr.tile_start;
+    const int b = local / per_pose;
+    const int tin = local - b * per_pose;
+    const int ty = tin / sr.tiles_x, tx = tin - ty * sr.tiles_x;
+    {
+      const unsigned int* src = reinterpret_cast<const unsigned int*>(sr.geom + b);
+      unsigned int* dst = reinterpret_cast<unsigned int*>(&spg);
+      for (int i = threadIdx.x; i < static_cast<int>(sizeof(PoseGeom) / 4); i += kThreads) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int w = tx * kTileW + (warp & 3) * kWarpTileW + (lane & 7);
+    const int h = ty * kTileH + (warp >> 2) * kWarpTileH + (lane >> 3);
+    const bool valid = (w < sr.det.W) && (h < sr.det.H);
+    const size_t npix = static_cast<size_t>(sr.det.H) * sr.det.W;
+    const size_t pix = static_cast<size_t>(h) * sr.det.W + w;
+    const bool want_grad = sr.grad != nullptr;
+    RayResult res;
+    res.F = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) res.J[k] = 0.f;
+    float gsc = 0.f;
+    if (valid) {
+      if (want_grad) {
+        gsc = sr.grad[b * npix + pix];
+        serve_trace<kPoseGrad>(sr.vd, spg, h, w, gsc, res);
+      } else {
+        serve_trace<kFwd>(sr.vd, spg, h, w, 0.f, res);
+      }
+      sr.out[b * npix + pix] = res.F;
+    }
+    if (want_grad) {  // uniform across the block
+      float c[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) c[k] = gsc * res.J[k];
+      block_sum6(c, red);
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sr.partials[(static_cast<size_t>(b) * per_pose + tin) * 6 + k] = c[k];
+      }
+    }
+    __syncthreads();  // shared request / pose data is rewritten for the next tile
+  }
+}
+
+// Fixed-order FP64 sum of each gradient request's per-tile partials: one warp per pose.
+__global__ void serve_finalize_kernel(const ServeHeader* __restrict__ hdr, const ServeRequest* __restrict__ reqs) {
+  const int nreq = hdr->nreq, total = hdr->total_poses;
+  const int lane = threadIdx.x & 31;
+  for (int i = blockIdx.x; i < total; i += gridDim.x) {
+    const int r = find_request(reqs, nreq, i, false);
+    const ServeRequest& q = reqs[r];
+    if (q.grad == nullptr) continue;
+    const int b = i - q.pose_start;
+    const int nt = q.tiles_x * q.tiles_y;
+    for (int k = 0; k < 6; ++k) {
+      double s = 0.0;
+      for (int c = lane; c < nt; c += 32) s += static_cast<double>(q.partials[(static_cast<size_t>(b) * nt + c) * 6 + k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) q.grad_pose[6 * b + k] = static_cast<float>(s);
+    }
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   if (g > 152 * 64) g = 152 * 64;
@@ -734,6 +864,23 @@ cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, fl
 cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
                                const float* grad_drr, float* grad_vol, cudaStream_t stream) {
   return launch_siddon<kBackproject>(vd, det, pg, B, nullptr, nullptr, grad_drr, nullptr, grad_vol, stream);
+}
+
+int serve_walk_grid(int device) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, serve_walk_kernel, kThreads, 0);
+  return max(1, sms * max(per_sm, 1));
+}
+
+cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, int* counter, int max_poses,
+                              int walk_grid, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  serve_setup_kernel<<<max(1, (max_poses + 63) / 64), 64, 0, stream>>>(hdr, reqs);
+  serve_walk_kernel<<<walk_grid, kThreads, 0, stream>>>(hdr, reqs, counter);
+  serve_finalize_kernel<<<max(1, min(max_poses, 4096)), 32, 0, stream>>>(hdr, reqs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_abs_max(const void* src, int src_dtype, int64_t count, float mu_water, unsigned int* out_bits,

@@ -1,0 +1,569 @@
+// Continuous-batching request loop (include/drr.h, "serving").
+//
+// A host thread forms ticks.  Each tick admits queued requests in FIFO order
+// while request slots and the two explicit budgets (device buffers, pinned
+// staging) allow, stages their inputs, and runs one pose-setup, one persistent
+// ray-walk and one gradient-finalise launch covering all of their rays; the
+// three launches can be replayed from a CUDA graph captured at start-up (the
+// kernels read the tick's size from a device-resident table).  Up to two ticks
+// are in flight on the server's stream, so requests that arrive while a tick is
+// running are admitted into the next one.  A host function enqueued after each
+// tick's copies marks it finished; the loop then writes results into the
+// callers' buffers, frees the tick's memory and wakes the waiters.
+//
+// Nothing on the device waits on the host: there are no spin loops in the
+// kernels, so a stalled client cannot hang the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "drr.h"
+#include "drr_arena.h"
+#include "drr_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr size_t kAlign = 256;
+
+size_t up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+enum ReqState { kPending, kAdmitted, kDone };
+
+struct Req {
+  uint64_t id = 0;
+  drr_request r{};
+  drr::DetDev det{};
+  bool grad = false;
+  int tiles_x = 0, tiles_y = 0;
+  size_t npix = 0;
+  size_t dev_bytes = 0, host_bytes = 0;
+  size_t dev_off = 0, host_off = 0;
+  bool has_dev = false, has_host = false;
+  // device buffers (inside the device arena)
+  float *d_poses = nullptr, *d_grad = nullptr, *d_out = nullptr, *d_partials = nullptr, *d_gpose = nullptr;
+  drr::PoseGeom* d_geom = nullptr;
+  // pinned staging (inside the host arena)
+  float *h_poses = nullptr, *h_grad = nullptr, *h_out = nullptr, *h_gpose = nullptr;
+  Clock::time_point t_submit, t_admit, t_done;
+  int64_t tick = -1;
+  ReqState state = kPending;
+  drr_status status = DRR_OK;
+};
+
+struct Tick {
+  int64_t id = 0;
+  int set = 0;
+  std::vector<Req*> reqs;
+  cudaEvent_t start = nullptr, stop = nullptr;
+  std::atomic<bool> done{false};
+  struct drr_server_s* owner = nullptr;
+};
+
+// Sizes of a request's device and staging buffers (each piece 256-B aligned).
+void size_request(Req& q) {
+  const size_t B = static_cast<size_t>(q.r.B);
+  const size_t nt = static_cast<size_t>(q.tiles_x) * q.tiles_y;
+  q.dev_bytes = up(B * 6 * 4) + up(B * q.npix * 4) + up(B * sizeof(drr::PoseGeom));
+  q.host_bytes = up(B * 6 * 4) + up(B * q.npix * 4);
+  if (q.grad) {
+    q.dev_bytes += up(B * q.npix * 4) + up(B * nt * 6 * 4) + up(B * 6 * 4);
+    q.host_bytes += up(B * q.npix * 4) + up(B * 6 * 4);
+  }
+}
+
+}  // namespace
+
+struct drr_server_s {
+  drr_server_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  char* dev_base = nullptr;
+  char* host_base = nullptr;
+  drr::OffsetArena* dev_arena = nullptr;
+  drr::OffsetArena* host_arena = nullptr;
+  struct Set {
+    char* h_table = nullptr;  // pinned: header + requests
+    char* d_table = nullptr;
+    int* d_counter = nullptr;
+    cudaGraphExec_t graph = nullptr;
+  } sets[2];
+  size_t table_bytes = 0;
+  int walk_grid = 1;
+
+  std::mutex mu;
+  std::condition_variable cv_loop, cv_done;
+  std::deque<Req*> pending;
+  std::unordered_map<uint64_t, Req*> reqs;
+  std::deque<Tick*> inflight;
+  std::vector<double> latencies;
+  int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, ticks = 0;
+  double gpu_busy_ms = 0.0;
+  int admitted = 0;
+  uint64_t next_id = 1;
+  int64_t next_tick = 0;
+  bool stop = false;
+  std::thread loop;
+
+  void run();
+  bool form_tick(std::unique_lock<std::mutex>& lk);
+  void finish_tick(Tick* t);
+  cudaError_t launch_kernels(int set);
+};
+
+namespace {
+
+// Runs on a CUDA runtime thread once the tick's stream work is complete.  It
+// takes no lock (so it never stalls the stream behind the loop thread); the
+// loop re-checks the flag at least every 200 us.
+void CUDART_CB tick_done(void* p) {
+  Tick* t = static_cast<Tick*>(p);
+  drr_server_s* s = t->owner;
+  t->done.store(true);
+  s->cv_loop.notify_all();
+}
+
+}  // namespace
+
+cudaError_t drr_server_s::launch_kernels(int set) {
+  Set& st = sets[set];
+  if (st.graph) return cudaGraphLaunch(st.graph, stream);
+  const auto* hdr = reinterpret_cast<const drr::ServeHeader*>(st.d_table);
+  const auto* rq = reinterpret_cast<const drr::ServeRequest*>(st.d_table + sizeof(drr::ServeHeader));
+  return drr::launch_serve_tick(hdr, rq, st.d_counter, cfg.max_tick_poses, walk_grid, stream);
+}
+
+// Admit requests (FIFO) into a new tick and enqueue it.  Called with lk held;
+// drops it while staging inputs and issuing CUDA calls.
+bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
+  std::vector<Req*> batch;
+  int poses = 0;
+  while (!pending.empty() && admitted + static_cast<int>(batch.size()) < cfg.max_inflight) {
+    Req* q = pending.front();
+    if (poses + q->r.B > cfg.max_tick_poses) break;
+    size_t doff = 0, hoff = 0;
+    if (!dev_arena->alloc(q->dev_bytes, &doff)) break;
+    if (!host_arena->alloc(q->host_bytes, &hoff)) {
+      dev_arena->release(doff);
+      break;
+    }
+    pending.pop_front();
+    q->dev_off = doff;
+    q->host_off = hoff;
+    q->has_dev = q->has_host = true;
+    q->state = kAdmitted;
+    q->t_admit = Clock::now();
+    poses += q->r.B;
+    batch.push_back(q);
+  }
+  if (batch.empty()) return false;
+  admitted += static_cast<int>(batch.size());
+  Tick* t = new Tick();
+  t->id = next_tick++;
+  t->set = static_cast<int>(t->id & 1);
+  t->owner = this;
+  t->reqs = batch;
+  lk.unlock();
+  cudaError_t e = cudaEventCreate(&t->start);
+  if (e == cudaSuccess) e = cudaEventCreate(&t->stop);
+
+  // carve the buffers and stage the inputs
+  Set& st = sets[t->set];
+  auto* hdr = reinterpret_cast<drr::ServeHeader*>(st.h_table);
+  auto* rq = reinterpret_cast<drr::ServeRequest*>(st.h_table + sizeof(drr::ServeHeader));
+  int tile_start = 0, pose_start = 0;
+  for (size_t i = 0; i < batch.size(); ++i) {
+    Req* q = batch[i];
+    q->tick = t->id;
+    const size_t B = static_cast<size_t>(q->r.B), nt = static_cast<size_t>(q->tiles_x) * q->tiles_y;
+    char* d = dev_base + q->dev_off;
+    char* h = host_base + q->host_off;
+    q->d_poses = reinterpret_cast<float*>(d); d += up(B * 6 * 4);
+    q->d_out = reinterpret_cast<float*>(d); d += up(B * q->npix * 4);
+    q->d_geom = reinterpret_cast<drr::PoseGeom*>(d); d += up(B * sizeof(drr::PoseGeom));
+    q->h_poses = reinterpret_cast<float*>(h); h += up(B * 6 * 4);
+    q->h_out = reinterpret_cast<float*>(h); h += up(B * q->npix * 4);
+    if (q->grad) {
+      q->d_grad = reinterpret_cast<float*>(d); d += up(B * q->npix * 4);
+      q->d_partials = reinterpret_cast<float*>(d); d += up(B * nt * 6 * 4);
+      q->d_gpose = reinterpret_cast<float*>(d);
+      q->h_grad = reinterpret_cast<float*>(h); h += up(B * q->npix * 4);
+      q->h_gpose = reinterpret_cast<float*>(h);
+    }
+    std::memcpy(q->h_poses, q->r.poses, B * 6 * 4);
+    if (q->grad) std::memcpy(q->h_grad, q->r.grad_drr, B * q->npix * 4);
+    drr::ServeRequest& sr = rq[i];
+    std::memset(&sr, 0, sizeof(sr));
+    sr.vd = q->r.volume->vd;
+    sr.det = q->det;
+    sr.poses = q->d_poses;
+    sr.grad = q->d_grad;
+    sr.out = q->d_out;
+    sr.partials = q->d_partials;
+    sr.grad_pose = q->d_gpose;
+    sr.geom = q->d_geom;
+    sr.B = q->r.B;
+    sr.tiles_x = q->tiles_x;
+    sr.tiles_y = q->tiles_y;
+    sr.tile_start = tile_start;
+    sr.pose_start = pose_start;
+    tile_start += static_cast<int>(B * nt);
+    pose_start += static_cast<int>(B);
+  }
+  hdr->nreq = static_cast<int>(batch.size());
+  hdr->total_tiles = tile_start;
+  hdr->total_poses = pose_start;
+  hdr->pad_ = 0;
+  const size_t tbytes = sizeof(drr::ServeHeader) + batch.size() * sizeof(drr::ServeRequest);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st.d_table, st.h_table, tbytes, cudaMemcpyHostToDevice, stream);
+  for (Req* q : batch) {
+    if (e != cudaSuccess) break;
+    e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->r.B) * 6 * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && q->grad)
+      e = cudaMemcpyAsync(q->d_grad, q->h_grad, size_t(q->r.B) * q->npix * 4, cudaMemcpyHostToDevice, stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(t->start, stream);
+  if (e == cudaSuccess) e = launch_kernels(t->set);
+  if (e == cudaSuccess) drr::count_launches(3);
+  if (e == cudaSuccess) e = cudaEventRecord(t->stop, stream);
+  for (Req* q : batch) {
+    if (e != cudaSuccess) break;
+    e = cudaMemcpyAsync(q->h_out, q->d_out, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && q->grad)
+      e = cudaMemcpyAsync(q->h_gpose, q->d_gpose, size_t(q->r.B) * 6 * 4, cudaMemcpyDeviceToHost, stream);
+  }
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(stream, tick_done, t);
+  if (e != cudaSuccess) {
+    // the tick could not be enqueued completely: let what was queued drain, then fail its requests
+    cudaStreamSynchronize(stream);
+    for (Req* q : batch) q->status = drr::cuda_error(e, "serving tick");
+    if (t->stop) cudaEventDestroy(t->stop);
+    t->stop = nullptr;
+    t->done.store(true);
+  }
+  lk.lock();
+  inflight.push_back(t);
+  ++ticks;
+  return true;
+}
+
+// Called with the lock held once the tick's device work and copies are done.
+void drr_server_s::finish_tick(Tick* t) {
+  if (t->start && t->stop) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t->start, t->stop) == cudaSuccess) gpu_busy_ms += ms;
+  }
+  if (t->start) cudaEventDestroy(t->start);
+  if (t->stop) cudaEventDestroy(t->stop);
+  for (Req* q : t->reqs) {
+    if (q->status == DRR_OK) {
+      std::memcpy(q->r.drr_out, q->h_out, size_t(q->r.B) * q->npix * 4);
+      if (q->grad) std::memcpy(q->r.grad_pose_out, q->h_gpose, size_t(q->r.B) * 6 * 4);
+      ++completed;
+    } else {
+      ++failed;
+    }
+    if (q->has_dev) dev_arena->release(q->dev_off);
+    if (q->has_host) host_arena->release(q->host_off);
+    q->has_dev = q->has_host = false;
+    q->t_done = Clock::now();
+    if (q->status == DRR_OK) latencies.push_back(ms_between(q->t_submit, q->t_done));
+    q->state = kDone;
+    q->r.volume->refs.fetch_sub(1);
+    --admitted;
+  }
+  delete t;
+  cv_done.notify_all();
+}
+
+void drr_server_s::run() {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lk(mu);
+  for (;;) {
+    while (!inflight.empty() && inflight.front()->done.load()) {
+      Tick* t = inflight.front();
+      inflight.pop_front();
+      finish_tick(t);
+    }
+    if (stop && inflight.empty()) break;
+    bool launched = false;
+    if (!stop && inflight.size() < 2 && !pending.empty()) launched = form_tick(lk);
+    if (!launched) {
+      cv_loop.wait_for(lk, std::chrono::microseconds(200), [this] {
+        return stop || (!inflight.empty() && inflight.front()->done.load()) ||
+               (inflight.size() < 2 && !pending.empty());
+      });
+    }
+  }
+}
+
+extern "C" {
+
+drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
+  if (!out) return drr::set_error(DRR_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  drr_server_config cfg{};
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.device_budget_bytes == 0) cfg.device_budget_bytes = size_t(512) << 20;
+  if (cfg.host_budget_bytes == 0) cfg.host_budget_bytes = cfg.device_budget_bytes;
+  if (cfg.max_inflight <= 0) cfg.max_inflight = 64;
+  if (cfg.max_tick_poses <= 0) cfg.max_tick_poses = 4096;
+  if (cfg.max_inflight > 4096 || cfg.max_tick_poses > (1 << 20))
+    return drr::set_error(DRR_ERR_INVALID, "max_inflight <= 4096 and max_tick_poses <= 2^20 required");
+  drr_server_s* s = new drr_server_s();
+  s->cfg = cfg;
+  cudaError_t e = cudaSuccess;
+  if (cfg.device >= 0) e = cudaSetDevice(cfg.device);
+  if (e == cudaSuccess) e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_base), cfg.device_budget_bytes);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_base), cfg.host_budget_bytes, 0);
+  s->table_bytes = sizeof(drr::ServeHeader) + size_t(cfg.max_inflight) * sizeof(drr::ServeRequest);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s->sets[i].h_table), s->table_bytes, 0);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->sets[i].d_table), s->table_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->sets[i].d_counter), sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->sets[i].d_table, 0, s->table_bytes);
+  }
+  if (e == cudaSuccess) s->walk_grid = drr::serve_walk_grid(s->device);
+  if (e == cudaSuccess && cfg.use_cuda_graph) {
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t le = s->launch_kernels(i);
+        e = cudaStreamEndCapture(s->stream, &g);
+        if (le != cudaSuccess) e = le;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&s->sets[i].graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+    }
+  }
+  if (e != cudaSuccess) {
+    drr_status st = drr::cuda_error(e, "drr_server_create");
+    for (auto& st2 : s->sets) {
+      if (st2.graph) cudaGraphExecDestroy(st2.graph);
+      if (st2.h_table) cudaFreeHost(st2.h_table);
+      if (st2.d_table) cudaFree(st2.d_table);
+      if (st2.d_counter) cudaFree(st2.d_counter);
+    }
+    if (s->dev_base) cudaFree(s->dev_base);
+    if (s->host_base) cudaFreeHost(s->host_base);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return st;
+  }
+  s->dev_arena = new drr::OffsetArena(cfg.device_budget_bytes, kAlign);
+  s->host_arena = new drr::OffsetArena(cfg.host_budget_bytes, kAlign);
+  s->loop = std::thread([s] { s->run(); });
+  *out = s;
+  return DRR_OK;
+}
+
+drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* ticket) {
+  if (!s || !req || !ticket) return drr::set_error(DRR_ERR_INVALID, "NULL argument");
+  drr_volume v = req->volume;
+  if (!v || !v->storage) return drr::set_error(DRR_ERR_INVALID, "request volume is NULL or destroyed");
+  if (v->device != s->device) return drr::set_error(DRR_ERR_INVALID, "volume lives on another device");
+  drr::DetDev dd;
+  if (drr_status st = drr::check_detector(&req->detector, &dd)) return st;
+  if (drr_status st = drr::check_geometry(v->vd, dd)) return st;
+  if (req->B <= 0 || req->B > s->cfg.max_tick_poses)
+    return drr::set_error(DRR_ERR_INVALID, "B must be in [1, %d]", s->cfg.max_tick_poses);
+  if (!req->poses || !req->drr_out) return drr::set_error(DRR_ERR_INVALID, "poses and drr_out are required");
+  if (req->grad_drr && !req->grad_pose_out)
+    return drr::set_error(DRR_ERR_INVALID, "grad_pose_out is required with grad_drr");
+  Req* q = new Req();
+  q->r = *req;
+  q->det = dd;
+  q->grad = req->grad_drr != nullptr;
+  q->tiles_x = (dd.W + drr::kTileW - 1) / drr::kTileW;
+  q->tiles_y = (dd.H + drr::kTileH - 1) / drr::kTileH;
+  q->npix = size_t(dd.H) * dd.W;
+  if (size_t(req->B) * q->tiles_x * q->tiles_y >= (size_t(1) << 30)) {
+    delete q;
+    return drr::set_error(DRR_ERR_INVALID, "request has too many tiles");
+  }
+  size_request(*q);
+  if (q->dev_bytes > s->cfg.device_budget_bytes || q->host_bytes > s->cfg.host_budget_bytes) {
+    size_t need = q->dev_bytes;
+    delete q;
+    return drr::set_error(DRR_ERR_OOM, "request needs %zu device bytes, more than the server budget", need);
+  }
+  q->t_submit = Clock::now();
+  v->refs.fetch_add(1);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      v->refs.fetch_sub(1);
+      delete q;
+      return drr::set_error(DRR_ERR_INVALID, "server is shutting down");
+    }
+    q->id = s->next_id++;
+    s->reqs[q->id] = q;
+    s->pending.push_back(q);
+    ++s->submitted;
+    *ticket = q->id;
+  }
+  s->cv_loop.notify_all();
+  return DRR_OK;
+}
+
+drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, drr_result* res) {
+  if (!s) return drr::set_error(DRR_ERR_INVALID, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return drr::set_error(DRR_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  Req* q = it->second;
+  auto ready = [q] { return q->state == kDone; };
+  if (timeout_ms < 0) {
+    s->cv_done.wait(lk, ready);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+    return drr::set_error(DRR_ERR_TIMEOUT, "ticket %llu not finished after %d ms", (unsigned long long)ticket,
+                          timeout_ms);
+  }
+  if (res) {
+    res->status = q->status;
+    res->queue_ms = q->tick >= 0 ? ms_between(q->t_submit, q->t_admit) : 0.0;
+    res->latency_ms = ms_between(q->t_submit, q->t_done);
+    res->tick = q->tick;
+  }
+  drr_status st = q->status;
+  s->reqs.erase(it);
+  delete q;
+  if (st != DRR_OK) return drr::set_error(st, "request %llu did not complete", (unsigned long long)ticket);
+  return DRR_OK;
+}
+
+drr_status drr_server_cancel(drr_server s, uint64_t ticket) {
+  if (!s) return drr::set_error(DRR_ERR_INVALID, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return drr::set_error(DRR_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  Req* q = it->second;
+  if (q->state != kPending) return drr::set_error(DRR_ERR_BUSY, "request already admitted");
+  s->pending.erase(std::find(s->pending.begin(), s->pending.end(), q));
+  q->state = kDone;
+  q->status = DRR_ERR_CANCELLED;
+  q->t_done = Clock::now();
+  q->r.volume->refs.fetch_sub(1);
+  ++s->cancelled;
+  s->cv_done.notify_all();
+  return DRR_OK;
+}
+
+drr_status drr_server_get_stats(drr_server s, drr_server_stats* out) {
+  if (!s || !out) return drr::set_error(DRR_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->cancelled = s->cancelled;
+  out->ticks = s->ticks;
+  out->pending = static_cast<int32_t>(s->pending.size());
+  out->inflight = s->admitted;
+  out->device_in_use = s->dev_arena->in_use();
+  out->device_budget = s->cfg.device_budget_bytes;
+  out->gpu_busy_ms = s->gpu_busy_ms;
+  if (!s->latencies.empty()) {
+    std::vector<double> v = s->latencies;
+    std::sort(v.begin(), v.end());
+    auto pct = [&v](double p) {
+      size_t i = static_cast<size_t>(p * (v.size() - 1) + 0.5);
+      return v[std::min(i, v.size() - 1)];
+    };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = v.back();
+    double sum = 0.0;
+    for (double x : v) sum += x;
+    out->mean_ms = sum / v.size();
+  }
+  return DRR_OK;
+}
+
+drr_status drr_server_destroy(drr_server s) {
+  if (!s) return DRR_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    for (Req* q : s->pending) {
+      q->state = kDone;
+      q->status = DRR_ERR_CANCELLED;
+      q->t_done = Clock::now();
+      q->r.volume->refs.fetch_sub(1);
+      ++s->cancelled;
+    }
+    s->pending.clear();
+  }
+  s->cv_loop.notify_all();
+  s->cv_done.notify_all();
+  if (s->loop.joinable()) s->loop.join();
+  cudaStreamSynchronize(s->stream);
+  for (auto& kv : s->reqs) delete kv.second;
+  s->reqs.clear();
+  for (auto& st : s->sets) {
+    if (st.graph) cudaGraphExecDestroy(st.graph);
+    if (st.h_table) cudaFreeHost(st.h_table);
+    if (st.d_table) cudaFree(st.d_table);
+    if (st.d_counter) cudaFree(st.d_counter);
+  }
+  cudaFree(s->dev_base);
+  cudaFreeHost(s->host_base);
+  cudaStreamDestroy(s->stream);
+  delete s->dev_arena;
+  delete s->host_arena;
+  delete s;
+  return DRR_OK;
+}
+
+// ---- the arena on its own ----------------------------------------------------
+
+struct drr_arena_s {
+  drr::OffsetArena a;
+  drr_arena_s(size_t c, size_t al) : a(c, al) {}
+};
+
+drr_status drr_arena_create(size_t capacity, size_t align, drr_arena* out) {
+  if (!out) return drr::set_error(DRR_ERR_INVALID, "out is NULL");
+  if (align & (align - 1)) return drr::set_error(DRR_ERR_INVALID, "align must be a power of two");
+  *out = new drr_arena_s(capacity, align);
+  return DRR_OK;
+}
+
+drr_status drr_arena_alloc(drr_arena a, size_t bytes, size_t* offset) {
+  if (!a || !offset) return drr::set_error(DRR_ERR_INVALID, "NULL argument");
+  if (!a->a.alloc(bytes, offset)) return drr::set_error(DRR_ERR_OOM, "no free run of %zu bytes", bytes);
+  return DRR_OK;
+}
+
+drr_status drr_arena_free(drr_arena a, size_t offset) {
+  if (!a) return drr::set_error(DRR_ERR_INVALID, "NULL argument");
+  if (!a->a.release(offset)) return drr::set_error(DRR_ERR_NOT_FOUND, "offset %zu is not allocated", offset);
+  return DRR_OK;
+}
+
+size_t drr_arena_in_use(drr_arena a) { return a ? a->a.in_use() : 0; }
+size_t drr_arena_largest_free(drr_arena a) { return a ? a->a.largest_free() : 0; }
+
+drr_status drr_arena_destroy(drr_arena a) {
+  delete a;
+  return DRR_OK;
+}
+
+}  // extern "C"

@@ -26,6 +26,9 @@ EXPORTS = (
     "drr_volume_create", "drr_volume_destroy", "drr_volume_info", "drr_render", "drr_render_backward",
     "drr_ray_setup", "drr_count_segments", "drr_profile_enable", "drr_profile_read", "drr_profile_reset",
     "drr_launch_count", "drr_stream_check", "drr_last_error", "drr_version",
+    "drr_server_create", "drr_server_submit", "drr_server_wait", "drr_server_cancel", "drr_server_get_stats",
+    "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
+    "drr_arena_largest_free", "drr_arena_destroy",
 )
 
 
@@ -43,6 +46,31 @@ class drr_detector(ctypes.Structure):
 class drr_volume_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("hu_mu_water", ctypes.c_float), ("layout", ctypes.c_int32),
                 ("brick", ctypes.c_int32 * 3)]
+
+
+class drr_server_config(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_size_t), ("host_budget_bytes", ctypes.c_size_t),
+                ("max_inflight", ctypes.c_int32), ("max_tick_poses", ctypes.c_int32),
+                ("use_cuda_graph", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class drr_request(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_void_p), ("detector", drr_detector), ("B", ctypes.c_int32),
+                ("poses", ctypes.c_void_p), ("grad_drr", ctypes.c_void_p), ("drr_out", ctypes.c_void_p),
+                ("grad_pose_out", ctypes.c_void_p)]
+
+
+class drr_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("tick", ctypes.c_int64)]
+
+
+class drr_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("ticks", ctypes.c_int64), ("pending", ctypes.c_int32),
+                ("inflight", ctypes.c_int32), ("device_in_use", ctypes.c_size_t),
+                ("device_budget", ctypes.c_size_t), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("gpu_busy_ms", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -81,10 +109,24 @@ def load(path: str = LIB_PATH):
                                          ctypes.POINTER(ctypes.c_int64)]
         lib.drr_profile_reset.argtypes = []
         lib.drr_launch_count.argtypes = []
+        lib.drr_server_create.argtypes = [ctypes.POINTER(drr_server_config), ctypes.POINTER(_vp)]
+        lib.drr_server_submit.argtypes = [_vp, ctypes.POINTER(drr_request), ctypes.POINTER(ctypes.c_uint64)]
+        lib.drr_server_wait.argtypes = [_vp, ctypes.c_uint64, _i32, ctypes.POINTER(drr_result)]
+        lib.drr_server_cancel.argtypes = [_vp, ctypes.c_uint64]
+        lib.drr_server_get_stats.argtypes = [_vp, ctypes.POINTER(drr_server_stats)]
+        lib.drr_server_destroy.argtypes = [_vp]
+        lib.drr_arena_create.argtypes = [ctypes.c_size_t, ctypes.c_size_t, ctypes.POINTER(_vp)]
+        lib.drr_arena_alloc.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        lib.drr_arena_free.argtypes = [_vp, ctypes.c_size_t]
+        lib.drr_arena_in_use.argtypes = [_vp]
+        lib.drr_arena_largest_free.argtypes = [_vp]
+        lib.drr_arena_destroy.argtypes = [_vp]
         for name in EXPORTS:
             if name not in ("drr_last_error", "drr_version"):
                 getattr(lib, name).restype = ctypes.c_int
         lib.drr_launch_count.restype = ctypes.c_int64
+        lib.drr_arena_in_use.restype = ctypes.c_size_t
+        lib.drr_arena_largest_free.restype = ctypes.c_size_t
         _lib = lib
         return lib
 
@@ -274,6 +316,108 @@ def launch_count() -> int:
 def stream_check(stream=None):
     lib = load()
     check(lib.drr_stream_check(_stream_ptr(stream)))
+
+
+class Arena:
+    """The serving loop's host-side offset allocator (no CUDA calls)."""
+
+    def __init__(self, capacity: int, align: int = 256):
+        self._lib = load()
+        self.h = ctypes.c_void_p()
+        check(self._lib.drr_arena_create(capacity, align, ctypes.byref(self.h)))
+
+    def alloc(self, nbytes: int) -> int:
+        off = ctypes.c_size_t()
+        check(self._lib.drr_arena_alloc(self.h, nbytes, ctypes.byref(off)))
+        return off.value
+
+    def free(self, offset: int):
+        check(self._lib.drr_arena_free(self.h, offset))
+
+    def in_use(self) -> int:
+        return int(self._lib.drr_arena_in_use(self.h))
+
+    def largest_free(self) -> int:
+        return int(self._lib.drr_arena_largest_free(self.h))
+
+    def close(self):
+        if self.h.value:
+            self._lib.drr_arena_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    __del__ = close
+
+
+class Ticket:
+    """A submitted request: owns its host buffers until wait() returns."""
+
+    def __init__(self, server, tid, out, grad_pose, keep):
+        self.server = server
+        self.id = tid
+        self.out = out
+        self.grad_pose = grad_pose
+        self._keep = keep
+        self.result = None
+
+    def wait(self, timeout_ms: int = -1):
+        res = drr_result()
+        st = self.server._lib.drr_server_wait(self.server.h, self.id, int(timeout_ms), ctypes.byref(res))
+        if st == 4:  # DRR_ERR_TIMEOUT: ticket still valid
+            raise DrrError(st, self.server._lib.drr_last_error().decode())
+        self.result = res
+        self._keep = None
+        if st != 0:
+            raise DrrError(st, self.server._lib.drr_last_error().decode())
+        return self.out, self.grad_pose
+
+    def cancel(self):
+        check(self.server._lib.drr_server_cancel(self.server.h, self.id))
+
+
+class Server:
+    """Continuous-batching request loop (drr_server_*): host buffers in, host buffers out."""
+
+    def __init__(self, device_budget: int = 512 << 20, host_budget: int = 0, max_inflight: int = 64,
+                 max_tick_poses: int = 4096, use_cuda_graph: bool = True, device: int = -1):
+        self._lib = load()
+        cfg = drr_server_config(device_budget, host_budget, max_inflight, max_tick_poses,
+                                1 if use_cuda_graph else 0, device)
+        self.h = ctypes.c_void_p()
+        check(self._lib.drr_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
+
+    def submit(self, volume: Volume, det, poses, grad=None) -> Ticket:
+        d = detector(det)
+        poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 6)
+        B = poses.shape[0]
+        out = np.empty((B, d.height, d.width), np.float32)
+        keep = [poses, out]
+        req = drr_request(volume.handle, d, B, poses.ctypes.data, None, out.ctypes.data, None)
+        gpose = None
+        if grad is not None:
+            grad = np.ascontiguousarray(grad, dtype=np.float32).reshape(B, d.height, d.width)
+            gpose = np.empty((B, 6), np.float32)
+            keep += [grad, gpose]
+            req.grad_drr = grad.ctypes.data
+            req.grad_pose_out = gpose.ctypes.data
+        tid = ctypes.c_uint64()
+        check(self._lib.drr_server_submit(self.h, ctypes.byref(req), ctypes.byref(tid)))
+        return Ticket(self, tid.value, out, gpose, keep)
+
+    def stats(self) -> dict:
+        st = drr_server_stats()
+        check(self._lib.drr_server_get_stats(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in drr_server_stats._fields_}
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            check(self._lib.drr_server_destroy(self.h))
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd():

@@ -105,29 +105,34 @@ def test_autograd_function(drr):
     assert grad_err(poses.grad.cpu().numpy(), G_ref).max() < GRAD_TOL
 
 
-def test_central_fd_on_gpu_is_close(drr):
-    # FP32 central differences of the GPU forward on a smooth phantom (no voxel noise, so E is
-    # smooth at the step size) -- a report-level check, looser than the oracle gate
+def test_central_fd_on_gpu_matches_oracle_fd(drr):
+    # FP32 central differences of the GPU forward at h = 1e-3 rad / 1e-2 mm against the same
+    # differences of the FP64 oracle.  At this step E is kinked at the voxel scale, so both
+    # differ from the point derivative (the oracle pins show that FD with h = 1e-7 matches
+    # it); what must agree is the GPU forward under perturbation.  The analytic gradient is
+    # checked against the oracle's elsewhere.
     cfg = inputs.TINY
     vol_np = inputs.ellipsoid_phantom(cfg["shape_zyx"], cfg["spacing"], seed=cfg["phantom_seed"])
     det = cfg["detector"]
     vol = drr.Volume(vol_np, cfg["spacing"])
+    ov = ovol(vol_np, cfg["spacing"])
     poses_np = inputs.random_poses(1, seed=cfg["pose_seed"])
     g_np = inputs.upstream_grad((1, det.height, det.width), seed=57)
-    g = torch.from_numpy(g_np).cuda()
     p0 = poses_np.astype(np.float64)
-    G = drr.render_backward(vol, det, torch.from_numpy(poses_np).cuda(), g).cpu().numpy()[0]
-    fd = np.zeros(6)
+    fd_gpu, fd_ref = np.zeros(6), np.zeros(6)
     for k in range(6):
         h = 1e-3 if k < 3 else 1e-2
         pp, pm = p0.copy(), p0.copy()
         pp[0, k] += h
         pm[0, k] -= h
-        Ep = drr.render(vol, det, torch.from_numpy(pp.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
-        Em = drr.render(vol, det, torch.from_numpy(pm.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
-        fd[k] = np.sum(g_np * (Ep - Em)) / (np.float64(np.float32(pp[0, k])) - np.float64(np.float32(pm[0, k])))
+        pp, pm = pp.astype(np.float32), pm.astype(np.float32)
+        den = np.float64(pp[0, k]) - np.float64(pm[0, k])
+        Ep = drr.render(vol, det, torch.from_numpy(pp).cuda()).cpu().numpy().astype(np.float64)
+        Em = drr.render(vol, det, torch.from_numpy(pm).cuda()).cpu().numpy().astype(np.float64)
+        fd_gpu[k] = np.sum(g_np * (Ep - Em)) / den
+        fd_ref[k] = np.sum(g_np * (oracle.render(ov, odet(det), pp) - oracle.render(ov, odet(det), pm))) / den
     for grp in (slice(0, 3), slice(3, 6)):
-        assert np.abs(fd[grp] - G[grp]).max() < 3e-2 * np.abs(G[grp]).max(), (fd, G)
+        assert np.abs(fd_gpu[grp] - fd_ref[grp]).max() < 1e-3 * np.abs(fd_ref[grp]).max(), (fd_gpu, fd_ref)
 
 
 def test_backprojection_adjoint_identity(drr):

@@ -1,0 +1,177 @@
+"""GPU tests of the continuous-batching request loop: results equal to the
+direct calls, identical alone and in a mix, admission by budget, timeouts,
+cancellation and argument errors (all failures made on the host)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_12737_gb300 import inputs
+from tests._parity import FP32_TOL, GRAD_TOL, grad_err, odet, ovol, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def drr():
+    from paper_2208_12737_gb300 import build
+    build.build()
+    from paper_2208_12737_gb300 import drr as d
+    d.load()
+    return d
+
+
+@pytest.fixture(scope="module")
+def vols(drr):
+    rng = np.random.default_rng(70)
+    a = inputs.ellipsoid_phantom((40, 48, 56), (1.2, 1.0, 1.1), seed=71)
+    hu = inputs.ct_phantom_hu((30, 64, 64), (1.3, 1.3, 3.0), seed=72)
+    c = rng.uniform(0, 0.03, (24, 20, 28)).astype(np.float32)
+    return {
+        "a": (a, (1.2, 1.0, 1.1), drr.Volume(a, (1.2, 1.0, 1.1))),
+        "hu": (hu, (1.3, 1.3, 3.0), drr.Volume(hu, (1.3, 1.3, 3.0), hu=True, storage="bf16")),
+        "c": (c, (0.9, 1.4, 1.0), drr.Volume(c, (0.9, 1.4, 1.0), storage="f16")),
+    }
+
+
+def _direct(drr, vol, det, poses_np, g_np=None):
+    poses = torch.from_numpy(poses_np).cuda()
+    if g_np is None:
+        return drr.render(vol, det, poses).cpu().numpy(), None
+    E, J = drr.render(vol, det, poses, jacobian=True)
+    G = drr.render_backward(vol, det, poses, torch.from_numpy(g_np).cuda())
+    return E.cpu().numpy(), G.cpu().numpy()
+
+
+def _mix(vols, seed, n):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        key = ["a", "hu", "c"][i % 3]
+        H, W = int(rng.integers(9, 70)), int(rng.integers(9, 70))
+        det = inputs.Detector(300.0, H, W, float(rng.uniform(1.0, 2.5)), float(rng.uniform(1.0, 2.5)))
+        B = int(rng.integers(1, 4))
+        poses = inputs.random_poses(B, seed=seed * 100 + i)
+        g = inputs.upstream_grad((B, H, W), seed=seed * 100 + i) if rng.uniform() < 0.5 else None
+        reqs.append((key, det, poses, g))
+    return reqs
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_server_matches_direct_calls(drr, vols, graph):
+    srv = drr.Server(device_budget=64 << 20, use_cuda_graph=graph)
+    reqs = _mix(vols, seed=1, n=12)
+    tickets = [srv.submit(vols[k][2], det, p, g) for (k, det, p, g) in reqs]
+    for (k, det, p, g), t in zip(reqs, tickets):
+        E, G = t.wait(20000)
+        E_d, G_d = _direct(drr, vols[k][2], det, p, g)
+        if g is None:
+            np.testing.assert_array_equal(E, E_d)  # the same forward walk
+        else:
+            np.testing.assert_array_equal(G, G_d)  # same re-trace, same per-tile partials and order
+            E_j, _ = drr.render(vols[k][2], det, torch.from_numpy(p).cuda(), jacobian=True)
+            np.testing.assert_array_equal(E, E_j.cpu().numpy())
+    st = srv.stats()
+    assert st["completed"] == 12 and st["failed"] == 0 and st["pending"] == 0
+    srv.close()
+
+
+def test_server_results_match_oracle(drr, vols):
+    srv = drr.Server(device_budget=64 << 20)
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 33, 47, 1.7, 1.6)
+    poses = inputs.random_poses(2, seed=73)
+    g = inputs.upstream_grad((2, 33, 47), seed=74)
+    E, G = srv.submit(vol, det, poses, g).wait(20000)
+    E_ref = oracle.render(ovol(data, sp), odet(det), poses)
+    G_ref = oracle.pose_grad(ovol(data, sp), odet(det), poses, g.astype(np.float64))
+    assert rel_err(E, E_ref).max() < FP32_TOL
+    assert grad_err(G, G_ref).max() < GRAD_TOL
+    srv.close()
+
+
+def test_alone_and_in_mix_are_identical(drr, vols):
+    probe = ("hu", inputs.Detector(300.0, 40, 52, 1.8, 1.8), inputs.random_poses(3, seed=75),
+             inputs.upstream_grad((3, 40, 52), seed=76))
+    srv = drr.Server(device_budget=128 << 20, max_inflight=16)
+    E1, G1 = srv.submit(vols[probe[0]][2], probe[1], probe[2], probe[3]).wait(20000)
+    # the same request in the middle of a stream of others (several ticks, mixed volumes)
+    mix = _mix(vols, seed=2, n=30)
+    tickets = [srv.submit(vols[k][2], d, p, g) for (k, d, p, g) in mix[:15]]
+    tp = srv.submit(vols[probe[0]][2], probe[1], probe[2], probe[3])
+    tickets += [srv.submit(vols[k][2], d, p, g) for (k, d, p, g) in mix[15:]]
+    E2, G2 = tp.wait(20000)
+    for t in tickets:
+        t.wait(20000)
+    np.testing.assert_array_equal(E1, E2)
+    np.testing.assert_array_equal(G1, G2)
+    assert srv.stats()["ticks"] >= 2
+    srv.close()
+
+
+def test_admission_by_budget(drr, vols):
+    # a budget that holds one 64x64 request at a time: the others queue and still complete
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 64, 64, 1.5, 1.5)
+    srv = drr.Server(device_budget=40 << 10, host_budget=40 << 10)
+    tickets = [srv.submit(vol, det, inputs.random_poses(2, seed=80 + i)) for i in range(6)]
+    outs = [t.wait(20000)[0] for t in tickets]
+    st = srv.stats()
+    assert st["completed"] == 6 and st["ticks"] >= 3  # never more than one request per tick fits
+    E_d, _ = _direct(drr, vol, det, inputs.random_poses(2, seed=85))
+    np.testing.assert_array_equal(outs[5], E_d)
+    # a request larger than the whole budget is refused up front
+    with pytest.raises(drr.DrrError) as ei:
+        srv.submit(vol, inputs.Detector(300.0, 200, 200, 0.5, 0.5), inputs.random_poses(4, seed=1))
+    assert ei.value.status == 2  # DRR_ERR_OOM
+    srv.close()
+
+
+def test_timeout_cancel_and_busy_volume(drr, vols):
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 64, 64, 1.5, 1.5)
+    srv = drr.Server(device_budget=40 << 10, host_budget=40 << 10)
+    tickets = [srv.submit(vol, det, inputs.random_poses(2, seed=90 + i)) for i in range(8)]
+    last = tickets[-1]
+    with pytest.raises(drr.DrrError) as ei:
+        last.wait(0)  # still queued behind the others
+    assert ei.value.status == 4  # DRR_ERR_TIMEOUT, the ticket stays valid
+    # a volume referenced by queued requests cannot be destroyed
+    with pytest.raises(drr.DrrError) as ei:
+        vol.close()
+    assert ei.value.status == 5  # DRR_ERR_BUSY
+    last.cancel()
+    with pytest.raises(drr.DrrError) as ei:
+        last.wait(1000)
+    assert ei.value.status == 8  # DRR_ERR_CANCELLED
+    for t in tickets[:-1]:
+        t.wait(20000)
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["completed"] == 7
+    srv.close()
+
+
+def test_malformed_requests(drr, vols):
+    data, sp, vol = vols["a"]
+    srv = drr.Server(device_budget=16 << 20)
+    with pytest.raises(drr.DrrError):
+        srv.submit(vol, inputs.Detector(300.0, 0, 10, 1.0, 1.0), inputs.random_poses(1, seed=1))
+    with pytest.raises(drr.DrrError):
+        srv.submit(vol, inputs.Detector(-3.0, 10, 10, 1.0, 1.0), inputs.random_poses(1, seed=1))
+    with pytest.raises(drr.DrrError):
+        srv.submit(vol, inputs.Detector(300.0, 10, 10, 1.0, 1.0), np.zeros((0, 6), np.float32))
+    t = srv.submit(vol, inputs.Detector(300.0, 10, 10, 1.0, 1.0), inputs.random_poses(1, seed=1))
+    t.wait(20000)
+    with pytest.raises(drr.DrrError) as ei:
+        t.wait(0)  # released
+    assert ei.value.status == 6  # DRR_ERR_NOT_FOUND
+    srv.close()
+
+
+def test_destroy_with_queued_requests(drr, vols):
+    data, sp, vol = vols["c"]
+    det = inputs.Detector(300.0, 64, 64, 1.5, 1.5)
+    srv = drr.Server(device_budget=40 << 10, host_budget=40 << 10)
+    tickets = [srv.submit(vol, det, inputs.random_poses(2, seed=100 + i)) for i in range(10)]
+    srv.close()  # drains what runs, cancels what waits
+    assert True
