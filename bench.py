@@ -150,6 +150,117 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serving_volumes(drr, hu133):
+    """The serving workload's 8 resident volumes: {128^3 @2 mm, 256^3 @1 mm, 512x512x133,
+    512x512x300} x {FP32, BF16}."""
+    from paper_2208_12737_gb300 import inputs
+    specs = [
+        ("128^3", lambda: (inputs.ellipsoid_phantom((128, 128, 128), (2.0, 2.0, 2.0), seed=81,
+                                                    semi_range=(10, 60), density_range=(0.0, 0.01)), False),
+         (2.0, 2.0, 2.0)),
+        ("256^3", lambda: (inputs.ellipsoid_phantom((256, 256, 256), (1.0, 1.0, 1.0), seed=82,
+                                                    semi_range=(10, 60), density_range=(0.0, 0.01)), False),
+         (1.0, 1.0, 1.0)),
+        ("512x512x133", lambda: (hu133, True), (0.703, 0.703, 2.5)),
+        ("512x512x300", lambda: (inputs.ct_phantom_hu((300, 512, 512), (0.703, 0.703, 1.1), seed=83), True),
+         (0.703, 0.703, 1.1)),
+    ]
+    vols = []
+    for name, make, sp in specs:
+        data, hu = make()
+        for storage in ("f32", "bf16"):
+            vols.append((f"{name}/{storage}", drr.Volume(data, sp, hu=hu, storage=storage)))
+    return vols
+
+
+def serve_bench(drr, hu133, seconds=4.0, seed=8, sat_requests=600):
+    """Served latency: saturation throughput, then Poisson arrivals at half of it."""
+    import threading
+    from paper_2208_12737_gb300 import inputs
+    vols = serving_volumes(drr, hu133)
+    rng = np.random.default_rng(seed)
+    grads = {}
+
+    def make_req():
+        name, v = vols[int(rng.integers(len(vols)))]
+        n = int(rng.integers(128, 513))
+        det = inputs.Detector(510.0, n, n, 280.0 / n, 280.0 / n)
+        pose = inputs.random_poses(1, seed=int(rng.integers(1 << 30)))
+        g = None
+        if rng.uniform() < 0.5:
+            if n not in grads:
+                grads[n] = inputs.upstream_grad((1, n, n), seed=n)
+            g = grads[n]
+        return v, det, pose, g
+
+    def drain(tickets, lat):
+        for t in tickets:
+            t.wait(120000)
+            lat.append(t.result.latency_ms)
+
+    # saturation: everything queued at once
+    reqs = [make_req() for _ in range(sat_requests)]
+    srv = drr.Server(device_budget=2 << 30, max_inflight=64, use_cuda_graph=True)
+    for r in reqs[:32]:  # warm-up
+        srv.submit(*r).wait(120000)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(*r) for r in reqs]
+    lat_sat = []
+    drain(tickets, lat_sat)
+    sat_rate = len(reqs) / (time.perf_counter() - t0)
+    srv.close()
+    # Poisson arrivals at half the saturation rate
+    rate = 0.5 * sat_rate
+    n_req = max(50, int(rate * seconds))
+    reqs = [make_req() for _ in range(n_req)]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    srv = drr.Server(device_budget=2 << 30, max_inflight=64, use_cuda_graph=True)
+    for r in reqs[:16]:
+        srv.submit(*r).wait(120000)
+    lat = []
+    queue = []
+    lock = threading.Condition()
+    done_flag = [False]
+
+    def waiter():
+        while True:
+            with lock:
+                while not queue and not done_flag[0]:
+                    lock.wait()
+                if not queue and done_flag[0]:
+                    return
+                t = queue.pop(0)
+            t.wait(120000)
+            lat.append(t.result.latency_ms)
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    for r, at in zip(reqs, arrivals):
+        while time.perf_counter() - t0 < at:
+            pass
+        tk = srv.submit(*r)
+        with lock:
+            queue.append(tk)
+            lock.notify()
+    with lock:
+        done_flag[0] = True
+        lock.notify()
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "requests": int(n_req), "offered_rate_per_s": rate,
+            "achieved_drrs_per_s": n_req / wall, "saturation_drrs_per_s": sat_rate,
+            "saturation_p50_ms": float(np.percentile(lat_sat, 50)), "ticks": int(st["ticks"]),
+            "gpu_busy_frac": st["gpu_busy_ms"] / 1e3 / wall,
+            "workload": "8 resident volumes {128^3, 256^3, 512x512x133, 512x512x300} x {FP32, BF16}; one pose per "
+                        "request; detector H=W~U{128..512} at 280/H mm, SDR 510; 50% render+pose-grad; Poisson "
+                        "arrivals at 50% of the measured saturation rate"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -279,6 +390,10 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    if not args.no_serve:
+        line["served"] = serve_bench(drr, hu, seconds=args.serve_seconds)
+        line["served_p50_ms"] = line["served"]["p50_ms"]
+        line["served_p99_ms"] = line["served"]["p99_ms"]
     if not args.no_cpu_baseline:
         cb, _, _ = cpu_oracle_sample(cfg, hu, poses_np, seconds_target=args.cpu_seconds)
         line["cpu_baseline"] = cb
@@ -296,6 +411,8 @@ def main():
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))

@@ -128,9 +128,11 @@ def test_admission_by_budget(drr, vols):
 
 
 def test_timeout_cancel_and_busy_volume(drr, vols):
+    # one slot and a long first request keep the later ones queued for milliseconds
     data, sp, vol = vols["a"]
+    srv = drr.Server(device_budget=256 << 20, max_inflight=1)
+    big = srv.submit(vol, inputs.Detector(300.0, 512, 512, 0.3, 0.3), inputs.random_poses(32, seed=89))
     det = inputs.Detector(300.0, 64, 64, 1.5, 1.5)
-    srv = drr.Server(device_budget=40 << 10, host_budget=40 << 10)
     tickets = [srv.submit(vol, det, inputs.random_poses(2, seed=90 + i)) for i in range(8)]
     last = tickets[-1]
     with pytest.raises(drr.DrrError) as ei:
@@ -144,10 +146,14 @@ def test_timeout_cancel_and_busy_volume(drr, vols):
     with pytest.raises(drr.DrrError) as ei:
         last.wait(1000)
     assert ei.value.status == 8  # DRR_ERR_CANCELLED
+    big.wait(60000)
     for t in tickets[:-1]:
-        t.wait(20000)
+        t.wait(60000)
     st = srv.stats()
-    assert st["cancelled"] == 1 and st["completed"] == 7
+    assert st["cancelled"] == 1 and st["completed"] == 8
+    with pytest.raises(drr.DrrError) as ei:
+        tickets[0].cancel()  # already finished and released
+    assert ei.value.status == 6
     srv.close()
 
 
