@@ -130,8 +130,8 @@ def test_admission_by_budget(drr, vols):
 def test_timeout_cancel_and_busy_volume(drr, vols):
     # one slot and a long first request keep the later ones queued for milliseconds
     data, sp, vol = vols["a"]
-    srv = drr.Server(device_budget=256 << 20, max_inflight=1)
-    big = srv.submit(vol, inputs.Detector(300.0, 512, 512, 0.3, 0.3), inputs.random_poses(32, seed=89))
+    srv = drr.Server(device_budget=300 << 20, max_inflight=1)
+    big = srv.submit(vol, inputs.Detector(300.0, 512, 512, 0.3, 0.3), inputs.random_poses(256, seed=89))
     det = inputs.Detector(300.0, 64, 64, 1.5, 1.5)
     tickets = [srv.submit(vol, det, inputs.random_poses(2, seed=90 + i)) for i in range(8)]
     last = tickets[-1]
