@@ -135,6 +135,26 @@ drr_status drr_render_backward(drr_volume v, const drr_detector* det, const floa
                                const float* grad_drr_dev, const float* jac_dev, float* grad_pose_dev,
                                float* grad_volume_dev, void* cuda_stream);
 
+/* Pose gradient from a stored Jacobian without allocating any device memory.
+ * The paper has no counterpart: this exists for callers that may not call
+ * cudaMalloc or cudaMallocAsync at all -- an application that fixes its whole
+ * device-memory footprint up front and forbids later allocations, or a plugin
+ * whose host framework owns every device allocation.
+ *  det, B, grad_drr_dev, jac_dev, grad_pose_dev: as for drr_render_backward with
+ *  a stored Jacobian and grad_volume_dev == NULL; the result is the same.
+ * The per-block partial sums live in one fixed array of device memory inside the
+ * library (1 MiB per GPU, held by every GPU that loads the library until the
+ * process exits), so B * ceil(H*W / 2048) * 6 must not exceed 262144; larger
+ * requests are rejected with DRR_ERR_INVALID and a message naming the limit.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before capturing a
+ * stream.  Every call uses the same array: calls whose work can overlap on the
+ * GPU (different streams without ordering between them) race and corrupt each
+ * other's results, so serialise them.  Nothing in the array needs clearing
+ * between calls: every partial sum is written before it is read. */
+drr_status drr_pose_grad_noalloc(const drr_detector* det, int32_t B, const float* grad_drr_dev,
+                                 const float* jac_dev, float* grad_pose_dev, void* cuda_stream);
+
 /* Ray setup alone (Sec. 2.4): for every pose and pixel write the source s
  * and pixel centre p in world coordinates, rays_out_dev = [B][H][W][6] float32
  * (sx, sy, sz, px, py, pz).  Used to test the geometry kernel. */

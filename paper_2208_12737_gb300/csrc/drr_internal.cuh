@@ -91,6 +91,9 @@ int pose_grad_blocks(const DetDev& det, bool from_jacobian);
 cudaError_t launch_pose_grad_partials(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
                                       const float* grad_drr, const float* jac, float* partials, cudaStream_t stream);
 cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream);
+// The stored-Jacobian half of launch_pose_grad_partials on its own.
+cudaError_t launch_jac_reduce(const DetDev& det, int B, const float* grad_drr, const float* jac, float* partials,
+                              cudaStream_t stream);
 cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, int* counts,
                                   cudaStream_t stream);
 cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,

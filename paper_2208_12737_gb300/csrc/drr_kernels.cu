@@ -856,6 +856,13 @@ cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const 
                                stream);
 }
 
+cudaError_t launch_jac_reduce(const DetDev& det, int B, const float* grad_drr, const float* jac, float* partials,
+                              cudaStream_t stream) {
+  dim3 grid(pose_grad_blocks(det, true), B);
+  jac_reduce_kernel<<<grid, kThreads, 0, stream>>>(grad_drr, jac, det.H * det.W, partials);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream) {
   pose_grad_finalize_kernel<<<B, 32, 0, stream>>>(partials, nblk, grad_pose);
   return cudaGetLastError();

@@ -28,7 +28,7 @@ EXPORTS = (
     "drr_launch_count", "drr_stream_check", "drr_last_error", "drr_version",
     "drr_server_create", "drr_server_submit", "drr_server_wait", "drr_server_cancel", "drr_server_get_stats",
     "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
-    "drr_arena_largest_free", "drr_arena_destroy",
+    "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc",
 )
 
 
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         lib.drr_arena_in_use.argtypes = [_vp]
         lib.drr_arena_largest_free.argtypes = [_vp]
         lib.drr_arena_destroy.argtypes = [_vp]
+        lib.drr_pose_grad_noalloc.argtypes = [ctypes.POINTER(drr_detector), _i32, _vp, _vp, _vp, _vp]
         for name in EXPORTS:
             if name not in ("drr_last_error", "drr_version"):
                 getattr(lib, name).restype = ctypes.c_int
