@@ -228,6 +228,9 @@ drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, dr
 /* Cancel a request that has not been admitted yet; DRR_ERR_BUSY once it has. */
 drr_status drr_server_cancel(drr_server s, uint64_t ticket);
 drr_status drr_server_get_stats(drr_server s, drr_server_stats* out);
+/* paused != 0: admit no new requests (queued ones wait; ticks already running
+ * finish), e.g. to drain the GPU for maintenance.  paused == 0 resumes. */
+drr_status drr_server_pause(drr_server s, int32_t paused);
 /* Finish in-flight ticks, cancel queued requests and free everything. */
 drr_status drr_server_destroy(drr_server s);
 

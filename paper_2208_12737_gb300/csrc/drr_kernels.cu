@@ -213,7 +213,7 @@ struct RaySetup {
 };
 
 constexpr unsigned int kExitUnits = 1u << 30;                    // the exit, in fixed-point units
-constexpr unsigned long long kNoCrossing64 = 0xC000000000000000ull;  // beyond any crossing of the ray
+constexpr unsigned long long kNoCrossing64 = 1ull << 63;  // beyond any crossing of the ray
 constexpr double kFixScale = 4611686018427387904.0;              // 2^62: fixed-point value of alpha = span
 
 // FP64 clip (Sec. 2.3, clamped to [0, 1]), entry/exit voxels and first
@@ -282,8 +282,9 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
     // first crossing, clamped into [0, span] (rounding can put it a hair outside)
     const double f = fmin(fmax((plane - ue) * rg[a], 0.0), span);
     r.A0[a] = r.cnt[a] > 0 ? static_cast<unsigned long long>(f * to_fix) : kNoCrossing64;
-    // plane spacing, saturated so that one step past the last plane cannot wrap
-    const double dfix = fmin(fabs(rg[a]) * to_fix, 2.0 * kFixScale);
+    // plane spacing, saturated at the span: an axis whose planes are farther
+    // apart has at most one crossing, and one step past it stays below 2^63
+    const double dfix = fmin(fabs(rg[a]) * to_fix, kFixScale);
     r.D[a] = static_cast<unsigned long long>(dfix);
     r.step[a] = up ? vd.stride[a] : -vd.stride[a];
   }
@@ -294,117 +295,230 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
 
 __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return static_cast<unsigned int>(x >> 32); }
 
-// Forward walk (Sec. 2.2 Siddon-Jacobs, Eq. 2): sum (a_{m+1} - a_m) V over the
-// ray, in fixed-point units.  The next voxel is loaded one iteration ahead of
-// its use.  An axis whose planes are used up can be picked once more only when
-// its next plane coincides with the exit to within a fixed-point unit; that
-// step lands in the zero padding and the remaining lengths are zero.
+// ---------------------------------------------------------------------------
+// Chunked walk.  The exact fixed-point crossing positions are the reference
+// frame, but the per-segment arithmetic runs in FP32 on positions measured from
+// a nearby origin: every kChunk segments the next crossing of each axis is
+// recomputed exactly (first + k * delta in 64-bit) relative to the exact
+// position of the current point, so local positions stay below ~kChunk plane
+// gaps and carry ~2^-29 of the span in absolute precision instead of the
+// 2^-24 * alpha of a whole-ray FP32 walk.  Positions are in fixed-point high-word
+// units (span / 2^30).
+// ---------------------------------------------------------------------------
+constexpr int kChunk = 16;
+constexpr float kTwoM32 = 2.3283064365386963e-10f;  // 2^-32
+
+// Per-thread exact crossing parameters, kept in shared memory: they are read
+// only when a chunk starts (and on the rare exact tie path).
+struct WalkScratch {
+  unsigned long long A0[3][kThreads];
+  unsigned long long D[3][kThreads];
+};
+
+__device__ __forceinline__ unsigned long long fix_at(unsigned long long A0, unsigned long long D, unsigned int k) {
+  return A0 + static_cast<unsigned long long>(k) * D;
+}
+
+// Local FP32 position (high-word units) of an exact position relative to O
+// (both below 2^64; the difference may be negative).
+__device__ __forceinline__ float local_pos(unsigned long long x, unsigned long long O) {
+  return x >= O ? static_cast<float>(x - O) * kTwoM32 : -static_cast<float>(O - x) * kTwoM32;
+}
+
 template <int DT>
-__device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetup& r) {
-  unsigned long long Ax = r.A0[0], Ay = r.A0[1], Az = r.A0[2];
+__device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetup& r, WalkScratch* ws) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ws->A0[a][t] = r.A0[a];
+    ws->D[a][t] = r.D[a];
+  }
+  const float dx = static_cast<float>(r.D[0]) * kTwoM32, dy = static_cast<float>(r.D[1]) * kTwoM32,
+              dz = static_cast<float>(r.D[2]) * kTwoM32;
+  unsigned int kx = 0u, ky = 0u, kz = 0u;  // crossings consumed per axis before this chunk
+  unsigned long long O = 0ull;              // exact position of the current point
   int off = r.off;
   float v = Voxel<DT>::load(vd.data, off);
   float acc = 0.f;
-  unsigned int ac = 0u;
-  for (int m = 1; m < r.nseg; ++m) {
-    const unsigned int hx = hi32(Ax), hy = hi32(Ay), hz = hi32(Az);
-    const unsigned int an = min(min(hx, hy), hz);
-    const bool bx = hx == an;
-    const bool by = !bx && hy == an;
-    const bool bz = !bx && !by;
-    off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
-    if (bx) Ax += r.D[0];
-    if (by) Ay += r.D[1];
-    if (bz) Az += r.D[2];
-    const float vn = Voxel<DT>::load(vd.data, off);
-    acc = fmaf(static_cast<float>(static_cast<int>(an - ac)), v, acc);
-    ac = an;
-    v = vn;
+  int remaining = r.nseg - 1;
+  for (;;) {
+    const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], kx), O);
+    const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], ky), O);
+    const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], kz), O);
+    float tx = x0, ty = y0, tz = z0;
+    float lx = 0.f, ly = 0.f, lz = 0.f;
+    float ac = 0.f;
+    const int n = min(remaining, kChunk);
+    for (int m = 0; m < n; ++m) {
+      const float an = fminf(fminf(tx, ty), tz);
+      const bool bx = tx == an;
+      const bool by = !bx && ty == an;
+      const bool bz = !bx && !by;
+      off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
+      if (bx) lx += 1.f;
+      if (by) ly += 1.f;
+      if (bz) lz += 1.f;
+      tx = fmaf(lx, dx, x0);
+      ty = fmaf(ly, dy, y0);
+      tz = fmaf(lz, dz, z0);
+      const float vn = Voxel<DT>::load(vd.data, off);
+      acc = fmaf(an - ac, v, acc);
+      ac = an;
+      v = vn;
+    }
+    remaining -= n;
+    kx += static_cast<unsigned int>(lx);
+    ky += static_cast<unsigned int>(ly);
+    kz += static_cast<unsigned int>(lz);
+    // the current point is the last crossing taken: the largest previous crossing
+    unsigned long long Onew = O;
+    if (kx) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], kx - 1u));
+    if (ky) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], ky - 1u));
+    if (kz) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], kz - 1u));
+    if (remaining == 0) {
+      acc = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O) - ac, v, acc);
+      break;
+    }
+    // keep the running sum exact across the re-anchoring: ac (local) becomes 0 at Onew
+    acc = fmaf(local_pos(Onew, O) - ac, v, acc);
+    O = Onew;
   }
-  acc = fmaf(static_cast<float>(static_cast<int>(kExitUnits - ac)), v, acc);
   return acc * r.unit;
 }
 
 // Walk with the pose-Jacobian bookkeeping (Sec. 2.4).  Crossing k with weight
 // w_k = V_before - V_after adds to per-axis sums G_a = sum w, A_a = sum w alpha
-// (alpha from the entry).  Only the two axes with fewer crossings are summed;
-// the third follows from sum_k w_k = 0 and sum_k w_k alpha_k = F over all
-// crossings, entry and exit included (end points clamped to alpha = 0 or 1
-// belong to no axis and are kept in Gc, Ac).  Crossings whose high words tie
-// are ordered by their full 64-bit values, which decides the voxel between
-// them and hence the weights.
+// (alpha from the entry).  The axes are relabelled per ray so that slot 2 is the
+// axis with most crossings; only slots 0 and 1 are summed and slot 2 follows
+// from sum_k w_k = 0 and sum_k w_k alpha_k = F over all crossings, entry and
+// exit included (end points clamped to alpha = 0 or 1 belong to no axis and are
+// kept in Gc, Ac).  When the two nearest crossings are within FP32 resolution
+// of each other their order -- which decides the voxel between them and hence
+// the weights -- is taken from the exact fixed-point positions.
 struct JacSums {
   float F, G[3], A[3], Gc, Ac;
   int dom;
 };
 
 template <int DT>
-__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, JacSums& out) {
+__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, WalkScratch* ws,
+                                              JacSums& out) {
+  constexpr float kTieUnits = 8.f;  // > twice the FP32 error of a local position (high-word units)
+  const int t = threadIdx.x;
   int dom = 0;
   if (r.cnt[1] > r.cnt[dom]) dom = 1;
   if (r.cnt[2] > r.cnt[dom]) dom = 2;
-  const int s0 = dom == 0 ? 1 : 0;  // the two summed axes
-  const int s1 = dom == 2 ? 1 : 2;
-  // slot per axis: 0 -> s0, 1 -> s1, 2 -> dom (not summed)
-  const int slx = s0 == 0 ? 0 : (s1 == 0 ? 1 : 2);
-  const int sly = s0 == 1 ? 0 : (s1 == 1 ? 1 : 2);
-  const int slz = s0 == 2 ? 0 : (s1 == 2 ? 1 : 2);
-  unsigned long long Ax = r.A0[0], Ay = r.A0[1], Az = r.A0[2];
+  const int a0 = dom == 0 ? 1 : 0;  // real axis of slot 0
+  const int a1 = dom == 2 ? 1 : 2;  // real axis of slot 1
+  const int ax_of[3] = {a0, a1, dom};
+  int step[3], cnt[3];
+  float dl[3];
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    const int a = ax_of[sl];
+    ws->A0[sl][t] = r.A0[a];
+    ws->D[sl][t] = r.D[a];
+    step[sl] = r.step[a];
+    cnt[sl] = r.cnt[a];
+    dl[sl] = static_cast<float>(r.D[a]) * kTwoM32;
+  }
+  unsigned int k0 = 0u, k1 = 0u, k2 = 0u;
+  unsigned long long O = 0ull;
   int off = r.off;
   float v = Voxel<DT>::load(vd.data, off);
-  float acc = 0.f, vprev = 0.f, acf = 0.f;
-  unsigned int ac = 0u;
+  float acc = 0.f, vprev = 0.f;
   float G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
-  int ps = r.ea == s0 ? 0 : (r.ea == s1 ? 1 : 2);  // slot of the crossing starting the current segment
-  if (r.ea < 0) Gc = -v;                           // entry clamped at alpha 0: weight -V_first
-  for (int m = 1; m < r.nseg; ++m) {
-    {  // the crossing that started the current segment (its voxel is known by now)
-      const float wgt = vprev - v;
-      if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, acf, A0); }
-      if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, acf, A1); }
+  // slot of the crossing that starts the current segment (2: not summed)
+  bool p0 = r.ea == a0, p1 = r.ea == a1;
+  if (r.ea < 0) Gc = -v;  // entry clamped at alpha 0: weight -V_first
+  float aprev = 0.f;      // absolute position (high-word units) of that crossing
+  int remaining = r.nseg - 1;
+  for (;;) {
+    const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], k0), O);
+    const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], k1), O);
+    const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], k2), O);
+    const float Of = static_cast<float>(O >> 32) + static_cast<float>(static_cast<unsigned int>(O)) * kTwoM32;
+    float tx = x0, ty = y0, tz = z0;
+    float lx = 0.f, ly = 0.f, lz = 0.f;
+    float ac = 0.f;
+    const int n = min(remaining, kChunk);
+    for (int m = 0; m < n; ++m) {
+      {  // the crossing that started the current segment (its voxel is known by now)
+        const float wgt = vprev - v;
+        if (p0) { G0 += wgt; A0 = fmaf(wgt, aprev, A0); }
+        if (p1) { G1 += wgt; A1 = fmaf(wgt, aprev, A1); }
+      }
+      const float mxy = fminf(tx, ty), Mxy = fmaxf(tx, ty);
+      const float an = fminf(mxy, tz);
+      const float second = fmaxf(mxy, fminf(Mxy, tz));
+      bool bx = tx == an;
+      bool by = !bx && ty == an;
+      if (second - an < kTieUnits) {
+        // near-coincident crossings: order them by their exact positions (rare)
+        const unsigned int kk[3] = {k0 + static_cast<unsigned int>(lx), k1 + static_cast<unsigned int>(ly),
+                                    k2 + static_cast<unsigned int>(lz)};
+        unsigned long long best = ~0ull;
+        int sel = 2;
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl) {
+          if (static_cast<int>(kk[sl]) < cnt[sl]) {
+            const unsigned long long e = fix_at(ws->A0[sl][t], ws->D[sl][t], kk[sl]);
+            if (e < best) { best = e; sel = sl; }
+          }
+        }
+        bx = sel == 0;
+        by = sel == 1;
+      }
+      const bool bz = !bx && !by;
+      const float a_new = bx ? tx : (by ? ty : tz);
+      off += bx ? step[0] : (by ? step[1] : step[2]);
+      if (bx) lx += 1.f;
+      if (by) ly += 1.f;
+      if (bz) lz += 1.f;
+      tx = fmaf(lx, dl[0], x0);
+      ty = fmaf(ly, dl[1], y0);
+      tz = fmaf(lz, dl[2], z0);
+      const float vn = Voxel<DT>::load(vd.data, off);
+      acc = fmaf(a_new - ac, v, acc);
+      ac = a_new;
+      aprev = Of + a_new;
+      p0 = bx;
+      p1 = by;
+      vprev = v;
+      v = vn;
     }
-    const unsigned int hx = hi32(Ax), hy = hi32(Ay), hz = hi32(Az);
-    const unsigned int mxy = min(hx, hy), Mxy = max(hx, hy);
-    const unsigned int an = min(mxy, hz);
-    const unsigned int second = max(mxy, min(Mxy, hz));
-    bool bx = hx == an;
-    bool by = !bx && hy == an;
-    if (second == an) {  // two crossings in one unit: compare the full values (rare)
-      const unsigned long long best = min(min(Ax, Ay), Az);
-      bx = Ax == best;
-      by = !bx && Ay == best;
+    remaining -= n;
+    k0 += static_cast<unsigned int>(lx);
+    k1 += static_cast<unsigned int>(ly);
+    k2 += static_cast<unsigned int>(lz);
+    unsigned long long Onew = O;
+    if (k0) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], k0 - 1u));
+    if (k1) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], k1 - 1u));
+    if (k2) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], k2 - 1u));
+    if (remaining == 0) {
+      acc = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O) - ac, v, acc);
+      break;
     }
-    const bool bz = !bx && !by;
-    off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
-    if (bx) Ax += r.D[0];
-    if (by) Ay += r.D[1];
-    if (bz) Az += r.D[2];
-    const float vn = Voxel<DT>::load(vd.data, off);
-    acc = fmaf(static_cast<float>(static_cast<int>(an - ac)), v, acc);
-    ac = an;
-    acf = static_cast<float>(static_cast<int>(an));
-    ps = bx ? slx : (by ? sly : slz);
-    vprev = v;
-    v = vn;
+    acc = fmaf(local_pos(Onew, O) - ac, v, acc);
+    O = Onew;
   }
   {
     const float wgt = vprev - v;
-    if (ps == 0) { G0 += wgt; A0 = fmaf(wgt, acf, A0); }
-    if (ps == 1) { G1 += wgt; A1 = fmaf(wgt, acf, A1); }
+    if (p0) { G0 += wgt; A0 = fmaf(wgt, aprev, A0); }
+    if (p1) { G1 += wgt; A1 = fmaf(wgt, aprev, A1); }
   }
-  acc = fmaf(static_cast<float>(static_cast<int>(kExitUnits - ac)), v, acc);
   // exit crossing: weight V_last - 0 at the exit
   const float ex = static_cast<float>(kExitUnits);
   float Ac = 0.f;
   if (r.xa < 0) { Gc += v; Ac = v * ex; }
-  else if (r.xa == s0) { G0 += v; A0 = fmaf(v, ex, A0); }
-  else if (r.xa == s1) { G1 += v; A1 = fmaf(v, ex, A1); }
+  else if (r.xa == a0) { G0 += v; A0 = fmaf(v, ex, A0); }
+  else if (r.xa == a1) { G1 += v; A1 = fmaf(v, ex, A1); }
   // back to alpha units
   const float u = r.unit;
   out.F = acc * u;
   out.dom = dom;
-  out.G[s0] = G0; out.A[s0] = A0 * u;
-  out.G[s1] = G1; out.A[s1] = A1 * u;
+  out.G[a0] = G0; out.A[a0] = A0 * u;
+  out.G[a1] = G1; out.A[a1] = A1 * u;
   out.G[dom] = -(G0 + G1 + Gc);  // sum of all crossing weights is 0
   out.A[dom] = 0.f;              // unused: the dominant axis is handled through R
   out.Gc = Gc;
@@ -498,7 +612,7 @@ __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RayS
 
 template <int MODE, int DT>
 __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gscale,
-                                          float* __restrict__ gvol, RayResult& res) {
+                                          float* __restrict__ gvol, WalkScratch* ws, RayResult& res) {
   res.F = 0.f;
   res.nseg = 0;
 #pragma unroll
@@ -516,10 +630,10 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
   if (MODE == kCount) return;
   const float L = sqrtf(r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2]);
   if (MODE == kFwd) {
-    res.F = walk_forward<DT>(vd, r) * L * vd.out_scale;
+    res.F = walk_forward<DT>(vd, r, ws) * L * vd.out_scale;
   } else if (MODE == kFwdJac || MODE == kPoseGrad) {
     JacSums s;
-    walk_jacobian<DT>(vd, r, s);
+    walk_jacobian<DT>(vd, r, ws, s);
     res.F = s.F * L * vd.out_scale;
     pose_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
   } else if (MODE == kBackproject) {
@@ -534,6 +648,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
                                                           float* __restrict__ partials, float* __restrict__ gvol) {
   __shared__ PoseGeom spg;
   __shared__ float red[kThreads / 32][6];
+  __shared__ WalkScratch ws;
   const int b = blockIdx.z;
   {
     const unsigned int* src = reinterpret_cast<const unsigned int*>(pgs + b);
@@ -553,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
   float gsc = 0.f;
   if (valid && (MODE == kPoseGrad || MODE == kBackproject)) gsc = gin[b * npix + pix];
   if (valid && !(MODE == kBackproject && gsc == 0.f)) {
-    trace_ray<MODE, DT>(vd, spg, h, w, gsc, gvol, r);
+    trace_ray<MODE, DT>(vd, spg, h, w, gsc, gvol, &ws, r);
   } else {
     r.F = 0.f;
 #pragma unroll
@@ -691,11 +806,11 @@ __global__ void serve_setup_kernel(const ServeHeader* __restrict__ hdr, const Se
 
 template <int MODE>
 __device__ __forceinline__ void serve_trace(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gsc,
-                                            RayResult& r) {
+                                            WalkScratch* ws, RayResult& r) {
   switch (vd.dtype) {
-    case kF32: trace_ray<MODE, kF32>(vd, pg, h, w, gsc, nullptr, r); break;
-    case kBF16: trace_ray<MODE, kBF16>(vd, pg, h, w, gsc, nullptr, r); break;
-    default: trace_ray<MODE, kF16>(vd, pg, h, w, gsc, nullptr, r); break;
+    case kF32: trace_ray<MODE, kF32>(vd, pg, h, w, gsc, nullptr, ws, r); break;
+    case kBF16: trace_ray<MODE, kBF16>(vd, pg, h, w, gsc, nullptr, ws, r); break;
+    default: trace_ray<MODE, kF16>(vd, pg, h, w, gsc, nullptr, ws, r); break;
   }
 }
 
@@ -708,6 +823,7 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
   __shared__ PoseGeom spg;
   __shared__ ServeRequest sr;
   __shared__ float red[kThreads / 32][6];
+  __shared__ WalkScratch ws;
   __shared__ int s_tile;
   const int nreq = hdr->nreq, total = hdr->total_tiles;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -748,9 +864,9 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
     if (valid) {
       if (want_grad) {
         gsc = sr.grad[b * npix + pix];
-        serve_trace<kPoseGrad>(sr.vd, spg, h, w, gsc, res);
+        serve_trace<kPoseGrad>(sr.vd, spg, h, w, gsc, &ws, res);
       } else {
-        serve_trace<kFwd>(sr.vd, spg, h, w, 0.f, res);
+        serve_trace<kFwd>(sr.vd, spg, h, w, 0.f, &ws, res);
       }
       sr.out[b * npix + pix] = res.F;
     }

@@ -117,6 +117,7 @@ struct drr_server_s {
   uint64_t next_id = 1;
   int64_t next_tick = 0;
   bool stop = false;
+  bool paused = false;
   std::thread loop;
 
   void run();
@@ -301,11 +302,11 @@ void drr_server_s::run() {
     }
     if (stop && inflight.empty()) break;
     bool launched = false;
-    if (!stop && inflight.size() < 2 && !pending.empty()) launched = form_tick(lk);
+    if (!stop && !paused && inflight.size() < 2 && !pending.empty()) launched = form_tick(lk);
     if (!launched) {
       cv_loop.wait_for(lk, std::chrono::microseconds(200), [this] {
         return stop || (!inflight.empty() && inflight.front()->done.load()) ||
-               (inflight.size() < 2 && !pending.empty());
+               (!paused && inflight.size() < 2 && !pending.empty());
       });
     }
   }
@@ -494,6 +495,16 @@ drr_status drr_server_get_stats(drr_server s, drr_server_stats* out) {
     for (double x : v) sum += x;
     out->mean_ms = sum / v.size();
   }
+  return DRR_OK;
+}
+
+drr_status drr_server_pause(drr_server s, int32_t paused) {
+  if (!s) return drr::set_error(DRR_ERR_INVALID, "server is NULL");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv_loop.notify_all();
   return DRR_OK;
 }
 

@@ -27,7 +27,7 @@ EXPORTS = (
     "drr_ray_setup", "drr_count_segments", "drr_profile_enable", "drr_profile_read", "drr_profile_reset",
     "drr_launch_count", "drr_stream_check", "drr_last_error", "drr_version",
     "drr_server_create", "drr_server_submit", "drr_server_wait", "drr_server_cancel", "drr_server_get_stats",
-    "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
+    "drr_server_pause", "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
     "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc",
 )
 
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         lib.drr_server_cancel.argtypes = [_vp, ctypes.c_uint64]
         lib.drr_server_get_stats.argtypes = [_vp, ctypes.POINTER(drr_server_stats)]
         lib.drr_server_destroy.argtypes = [_vp]
+        lib.drr_server_pause.argtypes = [_vp, _i32]
         lib.drr_arena_create.argtypes = [ctypes.c_size_t, ctypes.c_size_t, ctypes.POINTER(_vp)]
         lib.drr_arena_alloc.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
         lib.drr_arena_free.argtypes = [_vp, ctypes.c_size_t]
@@ -403,6 +404,10 @@ class Server:
         tid = ctypes.c_uint64()
         check(self._lib.drr_server_submit(self.h, ctypes.byref(req), ctypes.byref(tid)))
         return Ticket(self, tid.value, out, gpose, keep)
+
+    def pause(self, paused: bool = True):
+        """Stop (or resume) admitting queued requests; running ticks finish."""
+        check(self._lib.drr_server_pause(self.h, 1 if paused else 0))
 
     def stats(self) -> dict:
         st = drr_server_stats()
