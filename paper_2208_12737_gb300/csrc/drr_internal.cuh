@@ -12,13 +12,26 @@
 namespace drr {
 
 // Pixel tiling of the ray kernels: a 256-thread block covers 32 x 8 pixels,
-// each warp an 8 (columns) x 4 (rows) tile so that its 32 rays are spatial
-// neighbours and their voxel gathers share cache lines.
+// each warp a kWarpTileW x kWarpTileH tile (8 x 4 by default) so that its 32
+// rays are spatial neighbours and their voxel gathers share cache lines.
+#ifndef DRR_WARP_TILE_W
+#define DRR_WARP_TILE_W 8
+#endif
 constexpr int kThreads = 256;
 constexpr int kTileW = 32;
 constexpr int kTileH = 8;
-constexpr int kWarpTileW = 8;
-constexpr int kWarpTileH = 4;
+constexpr int kWarpTileW = DRR_WARP_TILE_W;
+constexpr int kWarpTileH = 32 / kWarpTileW;
+constexpr int kWarpsX = kTileW / kWarpTileW;
+static_assert(kWarpTileW >= 4 && kWarpTileW <= 32 && 32 % kWarpTileW == 0, "warp tile width");
+static_assert((kTileW / kWarpTileW) * (kTileH / kWarpTileH) == kThreads / 32, "8 warps per block tile");
+
+// Pixel of thread `tid` in block tile (tx, ty).
+__host__ __device__ __forceinline__ void tile_pixel(int tx, int ty, int tid, int* h, int* w) {
+  const int lane = tid & 31, warp = tid >> 5;
+  *w = tx * kTileW + (warp % kWarpsX) * kWarpTileW + lane % kWarpTileW;
+  *h = ty * kTileH + (warp / kWarpsX) * kWarpTileH + lane / kWarpTileW;
+}
 
 enum StorageType : int { kF32 = 0, kBF16 = 1, kF16 = 2 };
 

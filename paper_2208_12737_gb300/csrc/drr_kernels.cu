@@ -192,9 +192,9 @@ __device__ __forceinline__ void block_sum6(float v[6], float (*sm)[6]) {
 // Per-ray state after the FP64 setup: everything the walk needs.
 //
 // Crossing parameters are fixed point: alpha measured from the entry is held
-// as a 32.32 number in units of span / 2^30 (span = alpha_max - alpha_min), so
-// the high word of every crossing inside the ray lies in [0, 2^30] and the
-// exit is exactly 2^30.  Each axis' crossings form the arithmetic sequence
+// as a 32.32 number in units of span / 2^29 (span = alpha_max - alpha_min), so
+// the high word of every crossing inside the ray lies in [0, 2^29] and the
+// exit is exactly 2^29; every value the walk forms stays below 2^62.  Each axis' crossings form the arithmetic sequence
 // first + k * delta (Eq. 3), advanced by exact 64-bit additions: ordering is
 // exact to 2^-62 of the span and segment lengths are exact integers, so the
 // FP32 arithmetic is confined to the accumulation of length x density.
@@ -212,9 +212,9 @@ struct RaySetup {
   float d[3];                // p - s in mm
 };
 
-constexpr unsigned int kExitUnits = 1u << 30;                    // the exit, in fixed-point units
-constexpr unsigned long long kNoCrossing64 = 1ull << 63;  // beyond any crossing of the ray
-constexpr double kFixScale = 4611686018427387904.0;              // 2^62: fixed-point value of alpha = span
+constexpr unsigned int kExitUnits = 1u << 29;              // the exit, in high-word units
+constexpr unsigned long long kNoCrossing64 = 1ull << 62;  // beyond any crossing of the ray
+constexpr double kFixScale = 2305843009213693952.0;        // 2^61: fixed-point value of alpha = span
 
 // FP64 clip (Sec. 2.3, clamped to [0, 1]), entry/exit voxels and first
 // crossings.  Returns 1 for a hit, 0 when the ray misses, -1 for non-finite
@@ -283,7 +283,7 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
     const double f = fmin(fmax((plane - ue) * rg[a], 0.0), span);
     r.A0[a] = r.cnt[a] > 0 ? static_cast<unsigned long long>(f * to_fix) : kNoCrossing64;
     // plane spacing, saturated at the span: an axis whose planes are farther
-    // apart has at most one crossing, and one step past it stays below 2^63
+    // apart has at most one crossing, and one step past it stays below 2^62
     const double dfix = fmin(fabs(rg[a]) * to_fix, kFixScale);
     r.D[a] = static_cast<unsigned long long>(dfix);
     r.step[a] = up ? vd.stride[a] : -vd.stride[a];
@@ -305,7 +305,20 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 // 2^-24 * alpha of a whole-ray FP32 walk.  Positions are in fixed-point high-word
 // units (span / 2^30).
 // ---------------------------------------------------------------------------
-constexpr int kChunk = 16;
+#ifndef DRR_CHUNK
+#define DRR_CHUNK 16
+#endif
+#ifndef DRR_UNROLL
+#define DRR_UNROLL 1
+#endif
+#ifndef DRR_FWD_MINB
+#define DRR_FWD_MINB 6
+#endif
+#ifndef DRR_JAC_MINB
+#define DRR_JAC_MINB 4
+#endif
+constexpr int kChunk = DRR_CHUNK;
+constexpr int kUnroll = DRR_UNROLL;
 constexpr float kTwoM32 = 2.3283064365386963e-10f;  // 2^-32
 
 // Per-thread exact crossing parameters, kept in shared memory: they are read
@@ -319,10 +332,16 @@ __device__ __forceinline__ unsigned long long fix_at(unsigned long long A0, unsi
   return A0 + static_cast<unsigned long long>(k) * D;
 }
 
-// Local FP32 position (high-word units) of an exact position relative to O
-// (both below 2^64; the difference may be negative).
+// FP32 value (high-word units) of a signed 32.32 fixed-point number below 2^62
+// in magnitude, from two 32-bit conversions (a 64-bit conversion would run on
+// the FP64 pipe, which is narrow on this GPU).
+__device__ __forceinline__ float fix_to_float(long long d) {
+  return fmaf(static_cast<float>(static_cast<unsigned int>(d)), kTwoM32, static_cast<float>(static_cast<int>(d >> 32)));
+}
+
+// Local FP32 position of an exact position relative to O.
 __device__ __forceinline__ float local_pos(unsigned long long x, unsigned long long O) {
-  return x >= O ? static_cast<float>(x - O) * kTwoM32 : -static_cast<float>(O - x) * kTwoM32;
+  return fix_to_float(static_cast<long long>(x - O));
 }
 
 template <int DT>
@@ -333,8 +352,8 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
     ws->A0[a][t] = r.A0[a];
     ws->D[a][t] = r.D[a];
   }
-  const float dx = static_cast<float>(r.D[0]) * kTwoM32, dy = static_cast<float>(r.D[1]) * kTwoM32,
-              dz = static_cast<float>(r.D[2]) * kTwoM32;
+  const float dx = fix_to_float(static_cast<long long>(r.D[0])), dy = fix_to_float(static_cast<long long>(r.D[1])),
+              dz = fix_to_float(static_cast<long long>(r.D[2]));
   unsigned int kx = 0u, ky = 0u, kz = 0u;  // crossings consumed per axis before this chunk
   unsigned long long O = 0ull;              // exact position of the current point
   int off = r.off;
@@ -349,6 +368,7 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
     float lx = 0.f, ly = 0.f, lz = 0.f;
     float ac = 0.f;
     const int n = min(remaining, kChunk);
+#pragma unroll kUnroll
     for (int m = 0; m < n; ++m) {
       const float an = fminf(fminf(tx, ty), tz);
       const bool bx = tx == an;
@@ -420,7 +440,7 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     ws->D[sl][t] = r.D[a];
     step[sl] = r.step[a];
     cnt[sl] = r.cnt[a];
-    dl[sl] = static_cast<float>(r.D[a]) * kTwoM32;
+    dl[sl] = fix_to_float(static_cast<long long>(r.D[a]));
   }
   unsigned int k0 = 0u, k1 = 0u, k2 = 0u;
   unsigned long long O = 0ull;
@@ -437,11 +457,12 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], k0), O);
     const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], k1), O);
     const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], k2), O);
-    const float Of = static_cast<float>(O >> 32) + static_cast<float>(static_cast<unsigned int>(O)) * kTwoM32;
+    const float Of = fix_to_float(static_cast<long long>(O));
     float tx = x0, ty = y0, tz = z0;
     float lx = 0.f, ly = 0.f, lz = 0.f;
     float ac = 0.f;
     const int n = min(remaining, kChunk);
+#pragma unroll kUnroll
     for (int m = 0; m < n; ++m) {
       {  // the crossing that started the current segment (its voxel is known by now)
         const float wgt = vprev - v;
@@ -642,7 +663,8 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
 }
 
 template <int MODE, int DT>
-__global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGrad) ? 4 : 6) siddon_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs,
+__global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGrad) ? DRR_JAC_MINB : DRR_FWD_MINB)
+    siddon_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs,
                                                           float* __restrict__ out, float* __restrict__ jac,
                                                           const float* __restrict__ gin,
                                                           float* __restrict__ partials, float* __restrict__ gvol) {
@@ -656,9 +678,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(PoseGeom) / 4); i += kThreads) dst[i] = src[i];
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w = blockIdx.x * kTileW + (warp & 3) * kWarpTileW + (lane & 7);
-  const int h = blockIdx.y * kTileH + (warp >> 2) * kWarpTileH + (lane >> 3);
+  int h, w;
+  tile_pixel(blockIdx.x, blockIdx.y, threadIdx.x, &h, &w);
   const bool valid = (w < det.W) && (h < det.H);
   const size_t npix = static_cast<size_t>(det.H) * det.W;
   const size_t pix = static_cast<size_t>(h) * det.W + w;
@@ -826,7 +847,6 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
   __shared__ WalkScratch ws;
   __shared__ int s_tile;
   const int nreq = hdr->nreq, total = hdr->total_tiles;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
     __syncthreads();
@@ -850,8 +870,8 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
       for (int i = threadIdx.x; i < static_cast<int>(sizeof(PoseGeom) / 4); i += kThreads) dst[i] = src[i];
     }
     __syncthreads();
-    const int w = tx * kTileW + (warp & 3) * kWarpTileW + (lane & 7);
-    const int h = ty * kTileH + (warp >> 2) * kWarpTileH + (lane >> 3);
+    int h, w;
+    tile_pixel(tx, ty, threadIdx.x, &h, &w);
     const bool valid = (w < sr.det.W) && (h < sr.det.H);
     const size_t npix = static_cast<size_t>(sr.det.H) * sr.det.W;
     const size_t pix = static_cast<size_t>(h) * sr.det.W + w;
