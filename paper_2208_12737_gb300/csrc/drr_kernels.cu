@@ -306,18 +306,18 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 // units (span / 2^30).
 // ---------------------------------------------------------------------------
 #ifndef DRR_CHUNK
-#define DRR_CHUNK 16
+#define DRR_CHUNK 32
 #endif
 #ifndef DRR_UNROLL
-#define DRR_UNROLL 1
+#define DRR_UNROLL 8
 #endif
 #ifndef DRR_FWD_MINB
 #define DRR_FWD_MINB 6
 #endif
 #ifndef DRR_JAC_MINB
-#define DRR_JAC_MINB 4
+#define DRR_JAC_MINB 5
 #endif
-constexpr int kChunk = DRR_CHUNK;
+constexpr int kChunk = DRR_CHUNK;  // 32: local positions stay below ~32 plane gaps
 constexpr int kUnroll = DRR_UNROLL;
 constexpr float kTwoM32 = 2.3283064365386963e-10f;  // 2^-32
 
