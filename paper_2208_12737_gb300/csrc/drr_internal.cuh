@@ -44,6 +44,8 @@ struct PoseGeom {
   double g00[3];  // direction (p - s) / delta at pixel (h=0, w=0)
   double gw[3];   // change of the direction per detector column
   double gh[3];   // change of the direction per detector row
+  float u0f[3];   // FP32 copies of u0, un for the coarse clip
+  float unf[3];
   // Chain-rule terms for the pose Jacobian, world units (mm), j = angle index:
   float S[3][3];   // dR/d eta_j * s_c
   float Q[3][3];   // dR/d eta_j * (p_c(0,0) - s_c)

@@ -110,6 +110,8 @@ __device__ void compute_pose_geom(const float* pose, const DetDev& det, const Vo
     const double lo = -0.5 * static_cast<double>(vd.n[a]) * dl;  // b_a: volume centred at the origin
     g.u0[a] = (s[a] - lo) / dl;
     g.un[a] = static_cast<double>(vd.n[a]) - g.u0[a];
+    g.u0f[a] = static_cast<float>(g.u0[a]);
+    g.unf[a] = static_cast<float>(g.un[a]);
     g.g00[a] = (p00[a] - s[a]) / dl;
     g.gw[a] = ew[a] / dl;
     g.gh[a] = eh[a] / dl;
@@ -216,47 +218,80 @@ constexpr unsigned int kExitUnits = 1u << 29;              // the exit, in high-
 constexpr unsigned long long kNoCrossing64 = 1ull << 62;  // beyond any crossing of the ray
 constexpr double kFixScale = 2305843009213693952.0;        // 2^61: fixed-point value of alpha = span
 
+// Reciprocal of a double to ~1e-14 relative: an FP32 seed refined by one FP64
+// Newton step (a full FP64 division costs several times more on the FP64 pipe,
+// which is narrow on this GPU).  Exact division outside the FP32 seed's range.
+__device__ __forceinline__ double rcp_fast(double x) {
+  const float xf = static_cast<float>(x);
+  const float ax = fabsf(xf);
+  if (!(ax > 1e-30f && ax < 1e30f)) return 1.0 / x;
+  const double r = static_cast<double>(__frcp_rn(xf));
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// floor of a double: in FP32 unless the value is within 2^-10 of an integer
+// (or too large for FP32 to resolve that), where FP64 decides.
+__device__ __forceinline__ int floor_fast(double x) {
+  const float xf = static_cast<float>(x);
+  const float fl = floorf(xf);
+  const float fr = xf - fl;
+  if (fabsf(xf) < 4096.f && fr > 9.765625e-4f && fr < 1.f - 9.765625e-4f) return static_cast<int>(fl);
+  return static_cast<int>(floor(x));
+}
+
 // FP64 clip (Sec. 2.3, clamped to [0, 1]), entry/exit voxels and first
-// crossings.  Returns 1 for a hit, 0 when the ray misses, -1 for non-finite
-// geometry.
+// crossings.  The faces the ray enters and leaves through are found in FP32;
+// alpha_min / alpha_max are then evaluated in FP64 on those faces.  (Where two
+// faces tie to FP32 precision -- a ray through a box edge -- either choice
+// changes the entry by less than 1e-7 of alpha.)  Returns 1 for a hit, 0 when
+// the ray misses, -1 for non-finite geometry.
 __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg, int h, int w, RaySetup& r) {
   double g[3];
+  float gf[3];
   bool finite = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     g[a] = fma(static_cast<double>(h), pg.gh[a], fma(static_cast<double>(w), pg.gw[a], pg.g00[a]));
-    finite = finite && isfinite(g[a]) && isfinite(pg.u0[a]);
+    gf[a] = static_cast<float>(g[a]);
+    finite = finite && isfinite(gf[a]) && isfinite(pg.u0f[a]);
   }
   r.nseg = 0;
   if (!finite) return -1;
-  double amin = 0.0, amax = 1.0, rg[3];
+  float lof = 0.f, hif = 1.f;
   int ea = -1, xa = -1;
   bool hit = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (g[a] != 0.0) {
-      rg[a] = 1.0 / g[a];
-      const double t0 = -pg.u0[a] * rg[a], t1 = pg.un[a] * rg[a];
-      const double lo = fmin(t0, t1), hi = fmax(t0, t1);
-      if (lo > amin) { amin = lo; ea = a; }
-      if (hi < amax) { amax = hi; xa = a; }
-    } else {
-      rg[a] = 0.0;
-      if (!(pg.u0[a] >= 0.0 && pg.un[a] > 0.0)) hit = false;
+      const float rf = __frcp_rn(gf[a]);
+      const float t0 = -pg.u0f[a] * rf, t1 = pg.unf[a] * rf;
+      const float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
+      if (lo > lof) { lof = lo; ea = a; }
+      if (hi < hif) { hif = hi; xa = a; }
+    } else if (!(pg.u0[a] >= 0.0 && pg.un[a] > 0.0)) {
+      hit = false;
     }
   }
-  if (!hit || !(amin < amax)) return 0;
+  if (!hit || !(lof < hif)) return 0;
+  double rg[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) rg[a] = g[a] != 0.0 ? rcp_fast(g[a]) : 0.0;
+  // entry / exit faces: plane 0 when the ray runs up the axis, plane n otherwise
+  double amin = 0.0, amax = 1.0;
+  if (ea >= 0) amin = (g[ea] > 0.0 ? -pg.u0[ea] : pg.un[ea]) * rg[ea];
+  if (xa >= 0) amax = (g[xa] > 0.0 ? pg.un[xa] : -pg.u0[xa]) * rg[xa];
+  if (!(amin < amax)) return 0;
   r.ea = ea;
   r.xa = xa;
   r.amin = amin;
   const double span = amax - amin;
-  const double to_fix = kFixScale / span;  // fixed-point units per unit of alpha
-  r.unit = static_cast<float>(span / static_cast<double>(kExitUnits));
+  const double to_fix = kFixScale * rcp_fast(span);  // fixed-point units per unit of alpha
+  r.unit = static_cast<float>(span) * (1.f / static_cast<float>(kExitUnits));
   int total = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int n = vd.n[a];
-    r.d[a] = static_cast<float>(g[a] * static_cast<double>(vd.delta[a]));
+    r.d[a] = gf[a] * vd.delta[a];
     if (g[a] == 0.0) {
       r.ient[a] = min(max(static_cast<int>(floor(pg.u0[a])), 0), n - 1);
       r.cnt[a] = 0;
@@ -270,22 +305,21 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
     const double ux = fma(amax, g[a], pg.u0[a]);
     int i0, i1;
     if (a == ea) i0 = up ? 0 : n - 1;
-    else i0 = up ? static_cast<int>(floor(ue)) : static_cast<int>(ceil(ue)) - 1;
+    else i0 = up ? floor_fast(ue) : -floor_fast(-ue) - 1;
     if (a == xa) i1 = up ? n - 1 : 0;
-    else i1 = up ? static_cast<int>(ceil(ux)) - 1 : static_cast<int>(floor(ux));
+    else i1 = up ? -floor_fast(-ux) - 1 : floor_fast(ux);
     i0 = min(max(i0, 0), n - 1);
     i1 = min(max(i1, 0), n - 1);
     r.ient[a] = i0;
     r.cnt[a] = max(up ? i1 - i0 : i0 - i1, 0);
     total += r.cnt[a];
     const double plane = static_cast<double>(up ? i0 + 1 : i0);
-    // first crossing, clamped into [0, span] (rounding can put it a hair outside)
-    const double f = fmin(fmax((plane - ue) * rg[a], 0.0), span);
-    r.A0[a] = r.cnt[a] > 0 ? static_cast<unsigned long long>(f * to_fix) : kNoCrossing64;
+    // first crossing, kept within [0, span] (rounding can put it a hair outside)
+    const double f = fmax((plane - ue) * rg[a], 0.0);
+    r.A0[a] = r.cnt[a] > 0 ? min(__double2ull_rz(f * to_fix), 1ull << 61) : kNoCrossing64;
     // plane spacing, saturated at the span: an axis whose planes are farther
     // apart has at most one crossing, and one step past it stays below 2^62
-    const double dfix = fmin(fabs(rg[a]) * to_fix, kFixScale);
-    r.D[a] = static_cast<unsigned long long>(dfix);
+    r.D[a] = min(__double2ull_rz(fabs(rg[a]) * to_fix), 1ull << 61);
     r.step[a] = up ? vd.stride[a] : -vd.stride[a];
   }
   r.nseg = total + 1;
