@@ -299,3 +299,39 @@ def f16_scale(max_value: float) -> float:
         return 1.0
     _, e = np.frexp(np.float64(max_value))  # max = m 2^e, m in [0.5, 1)
     return float(2.0 ** (14 - int(e)))
+
+
+# ---------------------------------------------------------------------------
+# Registration loss (Sec. 3.2): negative zero-normalised cross-correlation.
+# Population statistics; I^ = (I - mean I) / (std I + eps), F^ likewise.
+# ---------------------------------------------------------------------------
+
+def zncc_loss(moving, fixed, eps: float = 1e-8):
+    """-mean(I^ F^) per image; moving, fixed: (B, ...) -> (B,) float64."""
+    I = np.asarray(moving, np.float64).reshape(len(moving), -1)
+    F = np.asarray(fixed, np.float64).reshape(len(fixed), -1)
+    Ic = I - I.mean(axis=1, keepdims=True)
+    Fc = F - F.mean(axis=1, keepdims=True)
+    Ih = Ic / (np.sqrt((Ic ** 2).mean(axis=1, keepdims=True)) + eps)
+    Fh = Fc / (np.sqrt((Fc ** 2).mean(axis=1, keepdims=True)) + eps)
+    return -(Ih * Fh).mean(axis=1)
+
+
+def zncc_loss_grad(moving, fixed, eps: float = 1e-8):
+    """d zncc_loss / d moving, by differentiating the definition term by term
+    (mean, centring, population std, normalisation, mean of the product)."""
+    shape = np.shape(moving)
+    I = np.asarray(moving, np.float64).reshape(shape[0], -1)
+    F = np.asarray(fixed, np.float64).reshape(shape[0], -1)
+    N = I.shape[1]
+    Ic = I - I.mean(axis=1, keepdims=True)
+    s = np.sqrt((Ic ** 2).mean(axis=1, keepdims=True))
+    Fc = F - F.mean(axis=1, keepdims=True)
+    Fh = Fc / (np.sqrt((Fc ** 2).mean(axis=1, keepdims=True)) + eps)
+    # loss = -(1/N) sum_i Fh_i Ic_i / (s + eps)
+    # d Ic_i / d I_j = delta_ij - 1/N ;  d s / d I_j = Ic_j / (N s)
+    dL_dIc = -Fh / (N * (s + eps))                                  # through the numerator
+    dL_ds = ((Fh * Ic).sum(axis=1, keepdims=True)) / (N * (s + eps) ** 2)
+    g = dL_dIc - dL_dIc.mean(axis=1, keepdims=True)                 # chain through the centring
+    g = g + dL_ds * np.where(s > 0, Ic / (N * np.where(s > 0, s, 1.0)), 0.0)
+    return g.reshape(shape)

@@ -94,3 +94,36 @@ def test_f16_scale_rule():
         assert 2.0 ** 13 <= m * sc < 2.0 ** 14
         assert np.log2(sc) == int(np.log2(sc))
     assert oracle.f16_scale(0.0) == 1.0
+
+
+def test_zncc_closed_forms():
+    rng = np.random.default_rng(36)
+    I = rng.uniform(0, 5, (3, 17, 13))
+    assert np.allclose(oracle.zncc_loss(I, I, eps=0.0), -1.0, atol=1e-14)
+    assert np.allclose(oracle.zncc_loss(I, 2.5 * I + 7.0, eps=0.0), -1.0, atol=1e-14)  # affine invariance
+    assert np.allclose(oracle.zncc_loss(I, -I, eps=0.0), 1.0, atol=1e-14)
+    J = rng.uniform(0, 5, (3, 17, 13))
+    L = oracle.zncc_loss(I, J, eps=0.0)
+    assert np.all(np.abs(L) < 1.0)
+    # symmetric in its arguments
+    assert np.allclose(L, oracle.zncc_loss(J, I, eps=0.0), atol=1e-14)
+
+
+def test_zncc_gradient():
+    rng = np.random.default_rng(37)
+    I = rng.uniform(0, 5, (2, 9, 11))
+    F = rng.uniform(0, 5, (2, 9, 11))
+    g = oracle.zncc_loss_grad(I, F, eps=1e-8)
+    # invariances (exact for eps = 0): adding a constant or scaling the moving image
+    # leaves the loss unchanged
+    g0 = oracle.zncc_loss_grad(I, F, eps=0.0)
+    assert np.allclose(g0.reshape(2, -1).sum(axis=1), 0.0, atol=1e-12)
+    assert np.allclose((g0 * I).reshape(2, -1).sum(axis=1), 0.0, atol=1e-12)
+    # central finite differences
+    h = 1e-6
+    for (b, i, j) in [(0, 0, 0), (1, 4, 7), (0, 8, 10)]:
+        Ip, Im = I.copy(), I.copy()
+        Ip[b, i, j] += h
+        Im[b, i, j] -= h
+        fd = (oracle.zncc_loss(Ip, F)[b] - oracle.zncc_loss(Im, F)[b]) / (2 * h)
+        assert abs(fd - g[b, i, j]) < 1e-7
