@@ -261,6 +261,36 @@ def serve_bench(drr, hu133, seconds=4.0, seed=8, sat_requests=600):
                         "arrivals at 50% of the measured saturation rate"}
 
 
+def registration_bench(drr, hu, lr_rot=1e-2, lr_trans=1.0):
+    """The registration workload: 64 concurrent registrations on the CT volume, 256x256
+    detector, initial offsets U(+-15 deg, +-20 mm) from seeded ground truths, -ZNCC with
+    Adam for 200 steps; convergence is -ZNCC < -0.999."""
+    import torch
+    from paper_2208_12737_gb300 import inputs
+    cfg = inputs.REGISTRATION
+    vol = drr.Volume(hu, cfg["spacing"], hu=True)
+    det = cfg["detector"]
+    B, steps = cfg["batch"], cfg["steps"]
+    truth = inputs.random_poses(B, seed=cfg["truth_seed"])
+    init = truth + inputs.pose_offsets(B, seed=cfg["offset_seed"])
+    fixed = drr.render(vol, det, torch.from_numpy(truth).cuda())
+    drr.register(vol, det, fixed, torch.from_numpy(init).cuda(), steps=3)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    poses, hist, first = drr.register(vol, det, fixed, torch.from_numpy(init).cuda(), steps=steps,
+                                      lr_rot=lr_rot, lr_trans=lr_trans)
+    dt = time.perf_counter() - t0
+    conv = first >= 0
+    err = poses - truth
+    return {"registrations": B, "steps": steps, "steps_per_s": steps / dt, "registration_steps_per_s": B * steps / dt,
+            "converged": int(conv.sum()), "mean_steps_to_converge": float(first[conv].mean()) if conv.any() else None,
+            "final_loss_median": float(np.median(hist[-1])),
+            "rot_err_deg_median": float(np.rad2deg(np.median(np.abs(err[:, :3])))),
+            "trans_err_mm_median": float(np.median(np.abs(err[:, 3:]))),
+            "optimizer": f"Adam lr_rot={lr_rot} rad, lr_trans={lr_trans} mm, betas (0.9, 0.999)",
+            "workload": "512x512x133 CT, 256x256 @1.4 mm, SDR 510; 64 problems, offsets U(+-15 deg, +-20 mm)"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -390,6 +420,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    if not args.no_registration:
+        line["registration"] = registration_bench(drr, hu)
     if not args.no_serve:
         line["served"] = serve_bench(drr, hu, seconds=args.serve_seconds)
         line["served_p50_ms"] = line["served"]["p50_ms"]
@@ -412,6 +444,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-registration", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -168,6 +168,29 @@ drr_status drr_ray_setup(const drr_detector* det, const float* poses_dev, int32_
 drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
                               int32_t* segments_out_dev, void* cuda_stream);
 
+/* ---- registration (Sec. 3.2: gradient descent on negative ZNCC) ---------- */
+
+/* Negative zero-normalised cross-correlation of B image pairs and its gradient
+ * with respect to the moving image (population statistics):
+ *   c = I - mean(I), s = sqrt(mean(c^2)), I^ = c / (s + eps), F^ likewise,
+ *   loss[b] = -mean(I^ F^)        (-1 for a perfect match, eps e.g. 1e-8).
+ *  moving_dev, fixed_dev : [B][npix] float32.
+ *  loss_dev              : NULL or [B] float32.
+ *  grad_dev              : NULL or [B][npix] float32, overwritten with d loss / d moving.
+ * Statistics are accumulated in FP64.  Errors: DRR_ERR_INVALID, DRR_ERR_CUDA. */
+drr_status drr_zncc(const float* moving_dev, const float* fixed_dev, int32_t B, int32_t npix, float eps,
+                    float* loss_dev, float* grad_dev, void* cuda_stream);
+
+/* One Adam step on B six-parameter poses, in place (the paper uses momentum
+ * gradient descent with separate rates for rotations and translations; Adam
+ * with the same split is used here):
+ *  params_dev, grads_dev, m_dev, v_dev : [B][6] float32 (m, v start at zero);
+ *  step : 1-based step count (bias correction); lr_rot for the three angles,
+ *  lr_trans for the three translations. */
+drr_status drr_adam_step(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev, int32_t B,
+                         int32_t step, float lr_rot, float lr_trans, float beta1, float beta2, float eps,
+                         void* cuda_stream);
+
 /* ---- serving: continuous batching of render / render+gradient requests ---- */
 /* No counterpart in the paper (whose method is a library call); this is the
  * request loop of the serving workload.  A host thread forms "ticks": it admits

@@ -28,7 +28,7 @@ EXPORTS = (
     "drr_launch_count", "drr_stream_check", "drr_last_error", "drr_version",
     "drr_server_create", "drr_server_submit", "drr_server_wait", "drr_server_cancel", "drr_server_get_stats",
     "drr_server_pause", "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
-    "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc",
+    "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc", "drr_zncc", "drr_adam_step",
 )
 
 
@@ -123,6 +123,9 @@ def load(path: str = LIB_PATH):
         lib.drr_arena_largest_free.argtypes = [_vp]
         lib.drr_arena_destroy.argtypes = [_vp]
         lib.drr_pose_grad_noalloc.argtypes = [ctypes.POINTER(drr_detector), _i32, _vp, _vp, _vp, _vp]
+        lib.drr_zncc.argtypes = [_vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _vp]
+        lib.drr_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]
         for name in EXPORTS:
             if name not in ("drr_last_error", "drr_version"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -313,6 +316,62 @@ def profile_read(kernel: str):
 
 def launch_count() -> int:
     return int(load().drr_launch_count())
+
+
+def zncc(moving, fixed, eps: float = 1e-8, grad: bool = True, stream=None):
+    """Negative ZNCC per image pair (B,) and, with grad=True, d loss / d moving (same shape)."""
+    import torch
+    lib = load()
+    B = moving.shape[0]
+    npix = moving[0].numel()
+    mp = _dev_ptr(moving, torch.float32, name="moving")
+    fp = _dev_ptr(fixed, torch.float32, tuple(moving.shape), "fixed")
+    loss = torch.empty((B,), device=moving.device, dtype=torch.float32)
+    g = torch.empty_like(moving) if grad else None
+    check(lib.drr_zncc(mp, fp, B, npix, float(eps), ctypes.c_void_p(loss.data_ptr()),
+                       ctypes.c_void_p(g.data_ptr()) if grad else None, _stream_ptr(stream)))
+    return (loss, g) if grad else loss
+
+
+def adam_step(params, grads, m, v, step: int, lr_rot: float, lr_trans: float, beta1: float = 0.9,
+              beta2: float = 0.999, eps: float = 1e-8, stream=None):
+    """In-place Adam update of (B, 6) pose parameters (separate rotation / translation rates)."""
+    import torch
+    lib = load()
+    B = params.shape[0]
+    ptrs = [_dev_ptr(t, torch.float32, (B, 6), n) for t, n in ((params, "params"), (grads, "grads"), (m, "m"),
+                                                                (v, "v"))]
+    check(lib.drr_adam_step(*ptrs, B, int(step), float(lr_rot), float(lr_trans), float(beta1), float(beta2),
+                            float(eps), _stream_ptr(stream)))
+
+
+def register(volume: Volume, det, fixed, init_poses, steps: int = 200, lr_rot: float = 1e-2, lr_trans: float = 1.0,
+             tol: float = -0.999, eps: float = 1e-8):
+    """Gradient registration (Sec. 3.2): minimise -ZNCC(DRR(pose), fixed) over the 6 pose parameters
+    of B independent problems with Adam.  Every step runs on the GPU: fused forward + Jacobian,
+    ZNCC loss and gradient, the pose-gradient reduction and the Adam update.
+
+    Returns (final poses (B, 6), loss history (steps, B), first step at which each problem reached
+    loss < tol or -1), all on the host."""
+    import torch
+    d = detector(det)
+    poses = init_poses.clone().contiguous().float()
+    B = poses.shape[0]
+    m = torch.zeros_like(poses)
+    v = torch.zeros_like(poses)
+    E = torch.empty((B, d.height, d.width), device=poses.device)
+    J = torch.empty((B, 6, d.height, d.width), device=poses.device)
+    hist = torch.empty((steps, B), device=poses.device)
+    for t in range(steps):
+        render(volume, d, poses, jacobian=True, out=E, jac=J)
+        loss, g = zncc(E, fixed, eps)
+        hist[t].copy_(loss)
+        G = render_backward(volume, d, poses, g, jac=J)
+        adam_step(poses, G, m, v, t + 1, lr_rot, lr_trans)
+    h = hist.cpu().numpy()
+    ok = h < tol
+    first = np.where(ok.any(axis=0), ok.argmax(axis=0), -1)
+    return poses.cpu().numpy(), h, first
 
 
 def stream_check(stream=None):

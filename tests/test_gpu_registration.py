@@ -1,0 +1,66 @@
+"""GPU tests of the registration pieces (Sec. 3.2): the ZNCC kernel against the
+FP64 oracle, the Adam kernel against its update rule, and end-to-end gradient
+registration that recovers ground-truth poses."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_12737_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def drr():
+    from paper_2208_12737_gb300 import build
+    build.build()
+    from paper_2208_12737_gb300 import drr as d
+    d.load()
+    return d
+
+
+def test_zncc_kernel_vs_oracle(drr):
+    rng = np.random.default_rng(111)
+    I = rng.uniform(0, 5, (5, 37, 41)).astype(np.float32)
+    F = (0.7 * I + rng.normal(0, 0.5, I.shape)).astype(np.float32)
+    loss, g = drr.zncc(torch.from_numpy(I).cuda(), torch.from_numpy(F).cuda(), eps=1e-8)
+    np.testing.assert_allclose(loss.cpu().numpy(), oracle.zncc_loss(I, F, 1e-8), rtol=1e-5, atol=1e-6)
+    g_ref = oracle.zncc_loss_grad(I, F, 1e-8)
+    assert np.abs(g.cpu().numpy() - g_ref).max() < 1e-5 * np.abs(g_ref).max()
+    # identical images: loss -1
+    l2 = drr.zncc(torch.from_numpy(I).cuda(), torch.from_numpy(I).cuda(), eps=1e-8, grad=False)
+    np.testing.assert_allclose(l2.cpu().numpy(), -1.0, atol=1e-6)
+
+
+def test_adam_kernel_update_rule(drr):
+    rng = np.random.default_rng(112)
+    p = rng.normal(size=(4, 6)).astype(np.float32)
+    P = torch.from_numpy(p.copy()).cuda()
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    pm, mm, vm = p.astype(np.float64), np.zeros((4, 6)), np.zeros((4, 6))
+    for t in range(1, 4):
+        g = rng.normal(size=(4, 6)).astype(np.float32)
+        drr.adam_step(P, torch.from_numpy(g).cuda(), m, v, t, 0.01, 0.5)
+        mm = 0.9 * mm + 0.1 * g
+        vm = 0.999 * vm + 0.001 * g.astype(np.float64) ** 2
+        lr = np.array([0.01] * 3 + [0.5] * 3)
+        pm = pm - lr * (mm / (1 - 0.9 ** t)) / (np.sqrt(vm / (1 - 0.999 ** t)) + 1e-8)
+    np.testing.assert_allclose(P.cpu().numpy(), pm, rtol=1e-5, atol=1e-6)
+
+
+def test_registration_recovers_poses(drr):
+    shape, sp = (60, 96, 96), (2.0, 2.0, 3.0)
+    hu = inputs.ct_phantom_hu(shape, sp, seed=113)
+    vol = drr.Volume(hu, sp, hu=True)
+    det = inputs.Detector(510.0, 96, 96, 3.0, 3.0)
+    truth = inputs.random_poses(6, seed=114, max_angle_deg=20, max_trans_mm=10)
+    fixed = drr.render(vol, det, torch.from_numpy(truth).cuda())
+    init = truth + inputs.pose_offsets(6, seed=115, max_angle_deg=4, max_trans_mm=4)
+    poses, hist, first = drr.register(vol, det, fixed, torch.from_numpy(init).cuda(), steps=150,
+                                      lr_rot=5e-3, lr_trans=0.5)
+    assert np.all(hist[-1] < -0.999), hist[-1]
+    assert np.all(first >= 0)
+    err = poses - truth
+    assert np.abs(err[:, :3]).max() < np.deg2rad(0.5) and np.abs(err[:, 3:]).max() < 1.0, err
