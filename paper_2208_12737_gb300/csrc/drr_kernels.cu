@@ -278,8 +278,11 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
   for (int a = 0; a < 3; ++a) rg[a] = g[a] != 0.0 ? rcp_fast(g[a]) : 0.0;
   // entry / exit faces: plane 0 when the ray runs up the axis, plane n otherwise
   double amin = 0.0, amax = 1.0;
-  if (ea >= 0) amin = (g[ea] > 0.0 ? -pg.u0[ea] : pg.un[ea]) * rg[ea];
-  if (xa >= 0) amax = (g[xa] > 0.0 ? pg.un[xa] : -pg.u0[xa]) * rg[xa];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {  // static indices: the arrays stay in registers
+    if (a == ea) amin = (g[a] > 0.0 ? -pg.u0[a] : pg.un[a]) * rg[a];
+    if (a == xa) amax = (g[a] > 0.0 ? pg.un[a] : -pg.u0[a]) * rg[a];
+  }
   if (!(amin < amax)) return 0;
   r.ea = ea;
   r.xa = xa;
@@ -360,7 +363,18 @@ constexpr float kTwoM32 = 2.3283064365386963e-10f;  // 2^-32
 struct WalkScratch {
   unsigned long long A0[3][kThreads];
   unsigned long long D[3][kThreads];
+  // Jacobian walk: state at the start of the current chunk, for its exact re-walk
+  int c_off[kThreads];
+  float c_v[kThreads], c_vprev[kThreads];
+  int c_pend[kThreads];
 };
+
+// x_a for a runtime axis index without indexing a register array (which
+// would move the array to local memory).
+template <class T>
+__device__ __forceinline__ T pick3(int a, T x0, T x1, T x2) {
+  return a == 0 ? x0 : (a == 1 ? x1 : x2);
+}
 
 __device__ __forceinline__ unsigned long long fix_at(unsigned long long A0, unsigned long long D, unsigned int k) {
   return A0 + static_cast<unsigned long long>(k) * D;
@@ -446,18 +460,29 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
 // axis with most crossings; only slots 0 and 1 are summed and slot 2 follows
 // from sum_k w_k = 0 and sum_k w_k alpha_k = F over all crossings, entry and
 // exit included (end points clamped to alpha = 0 or 1 belong to no axis and are
-// kept in Gc, Ac).  When the two nearest crossings are within FP32 resolution
-// of each other their order -- which decides the voxel between them and hence
-// the weights -- is taken from the exact fixed-point positions.
+// kept in Gc, Ac).
+//
+// The order of two crossings decides the voxel between them and hence both
+// weights, so it must be exact.  The FP32 walk of a chunk can only misorder
+// two crossings whose local positions lie within their rounding error
+// (<= 1.5 * 2^-23 of the position each), and then the walk takes a segment
+// shorter than that bound at the misordered pair.  So each chunk tracks its
+// shortest segment and the gap to the next crossing after it; if either is
+// below kTieRel * position + kTieAbs, the chunk is walked again from its saved
+// start state in exact fixed-point order (rare: a few chunks per thousand).
+// Sums are kept per chunk in local positions and moved to the anchor frame
+// when the chunk ends, so a re-walk only discards the chunk's own sums.
 struct JacSums {
   float F, G[3], A[3], Gc, Ac;
   int dom;
 };
 
+constexpr float kTieRel = 4.76837158203125e-7f;  // 2^-21 > twice 1.5 * 2^-23
+constexpr float kTieAbs = 4.f;                   // high-word units
+
 template <int DT>
 __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, WalkScratch* ws,
                                               JacSums& out) {
-  constexpr float kTieUnits = 8.f;  // > twice the FP32 error of a local position (high-word units)
   const int t = threadIdx.x;
   int dom = 0;
   if (r.cnt[1] > r.cnt[dom]) dom = 1;
@@ -470,48 +495,86 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     const int a = ax_of[sl];
-    ws->A0[sl][t] = r.A0[a];
-    ws->D[sl][t] = r.D[a];
-    step[sl] = r.step[a];
-    cnt[sl] = r.cnt[a];
-    dl[sl] = fix_to_float(static_cast<long long>(r.D[a]));
+    const unsigned long long D = pick3(a, r.D[0], r.D[1], r.D[2]);
+    ws->A0[sl][t] = pick3(a, r.A0[0], r.A0[1], r.A0[2]);
+    ws->D[sl][t] = D;
+    step[sl] = pick3(a, r.step[0], r.step[1], r.step[2]);
+    cnt[sl] = pick3(a, r.cnt[0], r.cnt[1], r.cnt[2]);
+    dl[sl] = fix_to_float(static_cast<long long>(D));
   }
-  unsigned int k0 = 0u, k1 = 0u, k2 = 0u;
-  unsigned long long O = 0ull;
+  unsigned int k0 = 0u, k1 = 0u, k2 = 0u;  // crossings taken per slot before this chunk
+  unsigned long long O = 0ull;              // exact position of the chunk's anchor
   int off = r.off;
   float v = Voxel<DT>::load(vd.data, off);
-  float acc = 0.f, vprev = 0.f;
-  float G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
-  // slot of the crossing that starts the current segment (2: not summed)
+  float vprev = 0.f;
+  float F = 0.f, G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
+  // slot of the crossing that starts the current segment (neither: slot 2 or a clamped entry)
   bool p0 = r.ea == a0, p1 = r.ea == a1;
   if (r.ea < 0) Gc = -v;  // entry clamped at alpha 0: weight -V_first
-  float aprev = 0.f;      // absolute position (high-word units) of that crossing
+  float last = 0.f;       // absolute position of the last crossing taken
   int remaining = r.nseg - 1;
   for (;;) {
+    const int n = min(remaining, kChunk);
+    ws->c_off[t] = off;
+    ws->c_v[t] = v;
+    ws->c_vprev[t] = vprev;
+    ws->c_pend[t] = p0 ? 0 : (p1 ? 1 : 2);
     const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], k0), O);
     const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], k1), O);
     const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], k2), O);
-    const float Of = fix_to_float(static_cast<long long>(O));
     float tx = x0, ty = y0, tz = z0;
     float lx = 0.f, ly = 0.f, lz = 0.f;
-    float ac = 0.f;
-    const int n = min(remaining, kChunk);
+    // chunk sums in local positions; the pending crossing sits at the anchor (0)
+    float ac = 0.f, f = 0.f, g0 = 0.f, g1 = 0.f, h0 = 0.f, h1 = 0.f;
+    float gmin = 3.0e38f;
 #pragma unroll kUnroll
     for (int m = 0; m < n; ++m) {
       {  // the crossing that started the current segment (its voxel is known by now)
         const float wgt = vprev - v;
-        if (p0) { G0 += wgt; A0 = fmaf(wgt, aprev, A0); }
-        if (p1) { G1 += wgt; A1 = fmaf(wgt, aprev, A1); }
+        if (p0) { g0 += wgt; h0 = fmaf(wgt, ac, h0); }
+        if (p1) { g1 += wgt; h1 = fmaf(wgt, ac, h1); }
       }
-      const float mxy = fminf(tx, ty), Mxy = fmaxf(tx, ty);
-      const float an = fminf(mxy, tz);
-      const float second = fmaxf(mxy, fminf(Mxy, tz));
-      bool bx = tx == an;
-      bool by = !bx && ty == an;
-      if (second - an < kTieUnits) {
-        // near-coincident crossings: order them by their exact positions (rare)
-        const unsigned int kk[3] = {k0 + static_cast<unsigned int>(lx), k1 + static_cast<unsigned int>(ly),
-                                    k2 + static_cast<unsigned int>(lz)};
+      const float an = fminf(fminf(tx, ty), tz);
+      const bool bx = tx == an;
+      const bool by = !bx && ty == an;
+      const bool bz = !bx && !by;
+      off += bx ? step[0] : (by ? step[1] : step[2]);
+      if (bx) lx += 1.f;
+      if (by) ly += 1.f;
+      if (bz) lz += 1.f;
+      tx = fmaf(lx, dl[0], x0);
+      ty = fmaf(ly, dl[1], y0);
+      tz = fmaf(lz, dl[2], z0);
+      const float vn = Voxel<DT>::load(vd.data, off);
+      const float seg = an - ac;
+      gmin = fminf(gmin, seg);
+      f = fmaf(seg, v, f);
+      ac = an;
+      p0 = bx;
+      p1 = by;
+      vprev = v;
+      v = vn;
+    }
+    unsigned int c0 = static_cast<unsigned int>(lx), c1 = static_cast<unsigned int>(ly),
+                 c2 = static_cast<unsigned int>(lz);
+    const float next = fminf(fminf(tx, ty), tz);
+    const bool tie = gmin < fmaf(ac, kTieRel, kTieAbs) ||
+                     (remaining > n && next - ac < fmaf(next, kTieRel, kTieAbs));
+    if (tie) {
+      // exact re-walk of the chunk: candidates compared as 64-bit fixed point
+      off = ws->c_off[t];
+      v = ws->c_v[t];
+      vprev = ws->c_vprev[t];
+      const int pend = ws->c_pend[t];
+      p0 = pend == 0;
+      p1 = pend == 1;
+      ac = f = g0 = g1 = h0 = h1 = 0.f;
+      c0 = c1 = c2 = 0u;
+      for (int m = 0; m < n; ++m) {
+        const float wgt = vprev - v;
+        if (p0) { g0 += wgt; h0 = fmaf(wgt, ac, h0); }
+        if (p1) { g1 += wgt; h1 = fmaf(wgt, ac, h1); }
+        const unsigned int kk[3] = {k0 + c0, k1 + c1, k2 + c2};
         unsigned long long best = ~0ull;
         int sel = 2;
 #pragma unroll
@@ -521,46 +584,49 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
             if (e < best) { best = e; sel = sl; }
           }
         }
-        bx = sel == 0;
-        by = sel == 1;
+        const bool sx = sel == 0, sy = sel == 1;
+        off += sx ? step[0] : (sy ? step[1] : step[2]);
+        c0 += sx ? 1u : 0u;
+        c1 += sy ? 1u : 0u;
+        c2 += (!sx && !sy) ? 1u : 0u;
+        const float an = local_pos(best, O);
+        const float vn = Voxel<DT>::load(vd.data, off);
+        f = fmaf(an - ac, v, f);
+        ac = an;
+        p0 = sx;
+        p1 = sy;
+        vprev = v;
+        v = vn;
       }
-      const bool bz = !bx && !by;
-      const float a_new = bx ? tx : (by ? ty : tz);
-      off += bx ? step[0] : (by ? step[1] : step[2]);
-      if (bx) lx += 1.f;
-      if (by) ly += 1.f;
-      if (bz) lz += 1.f;
-      tx = fmaf(lx, dl[0], x0);
-      ty = fmaf(ly, dl[1], y0);
-      tz = fmaf(lz, dl[2], z0);
-      const float vn = Voxel<DT>::load(vd.data, off);
-      acc = fmaf(a_new - ac, v, acc);
-      ac = a_new;
-      aprev = Of + a_new;
-      p0 = bx;
-      p1 = by;
-      vprev = v;
-      v = vn;
     }
     remaining -= n;
-    k0 += static_cast<unsigned int>(lx);
-    k1 += static_cast<unsigned int>(ly);
-    k2 += static_cast<unsigned int>(lz);
+    k0 += c0;
+    k1 += c1;
+    k2 += c2;
+    // chunk sums to the anchor frame: alpha = O + local
+    const float Of = fix_to_float(static_cast<long long>(O));
+    G0 += g0;
+    A0 += fmaf(Of, g0, h0);
+    G1 += g1;
+    A1 += fmaf(Of, g1, h1);
+    if (remaining == 0) {
+      F += fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O) - ac, v, f);
+      last = Of + ac;
+      break;
+    }
+    // the last crossing taken (the largest one) is the next anchor; the float
+    // position used for it in f is corrected to the exact one
     unsigned long long Onew = O;
     if (k0) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], k0 - 1u));
     if (k1) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], k1 - 1u));
     if (k2) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], k2 - 1u));
-    if (remaining == 0) {
-      acc = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O) - ac, v, acc);
-      break;
-    }
-    acc = fmaf(local_pos(Onew, O) - ac, v, acc);
+    F += fmaf(local_pos(Onew, O) - ac, v, f);
     O = Onew;
   }
-  {
+  {  // the last crossing taken
     const float wgt = vprev - v;
-    if (p0) { G0 += wgt; A0 = fmaf(wgt, aprev, A0); }
-    if (p1) { G1 += wgt; A1 = fmaf(wgt, aprev, A1); }
+    if (p0) { G0 += wgt; A0 = fmaf(wgt, last, A0); }
+    if (p1) { G1 += wgt; A1 = fmaf(wgt, last, A1); }
   }
   // exit crossing: weight V_last - 0 at the exit
   const float ex = static_cast<float>(kExitUnits);
@@ -570,12 +636,13 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
   else if (r.xa == a1) { G1 += v; A1 = fmaf(v, ex, A1); }
   // back to alpha units
   const float u = r.unit;
-  out.F = acc * u;
+  out.F = F * u;
   out.dom = dom;
-  out.G[a0] = G0; out.A[a0] = A0 * u;
-  out.G[a1] = G1; out.A[a1] = A1 * u;
-  out.G[dom] = -(G0 + G1 + Gc);  // sum of all crossing weights is 0
-  out.A[dom] = 0.f;              // unused: the dominant axis is handled through R
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {  // back to real axes (static indices)
+    out.G[a] = a == a0 ? G0 : (a == a1 ? G1 : -(G0 + G1 + Gc));  // sum of all crossing weights is 0
+    out.A[a] = a == a0 ? A0 * u : (a == a1 ? A1 * u : 0.f);      // the dominant axis is handled through R
+  }
   out.Gc = Gc;
   out.Ac = Ac * u;
 }
