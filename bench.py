@@ -89,12 +89,60 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload_inputs():
+def rank_batch(cfg, rank):
+    """The poses and upstream gradient one rank renders.  Poses are independent
+    problems, so N ranks each take their own batch of cfg["batch"] poses (weak
+    scaling, no data-path collective); rank 0's batch is the single-GPU one."""
+    from paper_2208_12737_gb300 import inputs
+    det = cfg["detector"]
+    poses = inputs.random_poses(cfg["batch"], seed=cfg["pose_seed"] + 1000 * rank)
+    g = inputs.upstream_grad((cfg["batch"], det.height, det.width), seed=3 + 1000 * rank)
+    return poses, g
+
+
+def max_over_ranks(values, dist=None, device=None):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the job time)."""
+    import torch
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(world, rays_per_rank, ms):
+    """Whole-job rays per second (G rays/s) when every rank renders rays_per_rank in ms."""
+    return world * rays_per_rank / (ms * 1e-3) / 1e9
+
+
+def kernel_source_hash():
+    """sha256 of the walk kernels' sources: a stored ncu traffic figure applies only to this source."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("drr_kernels.cu", "drr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2208_12737_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel="siddon_fwd_jac"):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    import glob
+    import re
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}__*.md"))):
+        with open(path) as f:
+            text = f.read()
+        m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source_sha256:\s*([0-9a-f]{64})", text)
+        if m and m.group(2) == kernel_source_hash():
+            return int(m.group(1))
+    return None
+
+
+def workload_inputs(rank=0):
     from paper_2208_12737_gb300 import inputs
     cfg = inputs.CT
     hu = inputs.ct_volume_hu()
-    poses = inputs.random_poses(cfg["batch"], seed=cfg["pose_seed"])
-    g = inputs.upstream_grad((cfg["batch"], cfg["detector"].height, cfg["detector"].width), seed=3)
+    poses, g = rank_batch(cfg, rank)
     return cfg, hu, poses, g
 
 
@@ -305,7 +353,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    cfg, hu, poses_np, g_np = workload_inputs()
+    cfg, hu, poses_np, g_np = workload_inputs(rank)
     det = cfg["detector"]
     B, H, W = cfg["batch"], det.height, det.width
     rays = B * H * W
@@ -379,15 +427,14 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     drr.profile_reset()
 
-    ms = statistics.mean(step_ms)
-    worst = torch.tensor([ms, statistics.mean(fwd_ms), statistics.mean(e2e_ms)], device=dev)
+    ms, fms, ems = max_over_ranks([statistics.mean(step_ms), statistics.mean(fwd_ms), statistics.mean(e2e_ms)],
+                                  dist, dev)
     if dist:
-        dist.all_reduce(worst, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms, fms, ems = worst.tolist()
     if rank != 0:
+        dist.destroy_process_group()
         return
-    value = world * rays / (ms * 1e-3) / 1e9
+    value = job_throughput(world, rays, ms)
     peaks, which = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     # dominant kernel: the fused forward + Jacobian walk; algorithmic work per launch
@@ -406,15 +453,15 @@ def run_ours(args, rank, world, local_rank):
                    "segments_per_step": int(seg), "storage": args.storage,
                    "step": "pose setup + fused Siddon fwd with per-ray pose Jacobian + g.J reduction",
                    "l2": "flushed (512 MB write) before every timed step, outside the timed events"},
-        "fwd_only": {"value": world * rays / (fms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": fms},
+        "fwd_only": {"value": job_throughput(world, rays, fms), "unit": UNIT, "ms_per_step": fms},
         "drrs_per_s": world * B / (ms * 1e-3),
         "segments_per_s": world * seg / (ms * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tops/s",
-                     "frac": achieved / peak_alu, "traffic": None,
+                     "frac": achieved / peak_alu, "traffic": profiled_traffic("siddon_fwd_jac"),
                      "kernel": "siddon_fwd_jac", "kernel_ms": k_ms,
                      "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({which} sm_max)",
                      "gathered_gbs": gather_gbs},
-        "e2e": {"value": world * rays / (ems * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": B * 6 * 4,
+        "e2e": {"value": job_throughput(world, rays, ems), "unit": UNIT, "h2d_bytes_per_step": B * 6 * 4,
                 "d2h_bytes_per_step": B * H * W * 4 + B * 6 * 4},
         "gpu_launches": int(launches),
         "clocks": clk,

@@ -352,7 +352,7 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 #define DRR_FWD_MINB 6
 #endif
 #ifndef DRR_JAC_MINB
-#define DRR_JAC_MINB 5
+#define DRR_JAC_MINB 4
 #endif
 constexpr int kChunk = DRR_CHUNK;  // 32: local positions stay below ~32 plane gaps
 constexpr int kUnroll = DRR_UNROLL;
@@ -363,7 +363,13 @@ constexpr float kTwoM32 = 2.3283064365386963e-10f;  // 2^-32
 struct WalkScratch {
   unsigned long long A0[3][kThreads];
   unsigned long long D[3][kThreads];
-  // Jacobian walk: state at the start of the current chunk, for its exact re-walk
+};
+// The Jacobian walk also keeps the state at the start of the current chunk,
+// for an exact re-walk of the chunk.  (Shared memory comes out of the same
+// on-chip store as the L1 cache that serves the voxel gathers, so each kernel
+// declares only what its walk uses.)
+struct JacScratch : WalkScratch {
+  int cnt[3][kThreads];  // crossings per slot (read only by the exact re-walk)
   int c_off[kThreads];
   float c_v[kThreads], c_vprev[kThreads];
   int c_pend[kThreads];
@@ -391,6 +397,19 @@ __device__ __forceinline__ float fix_to_float(long long d) {
 __device__ __forceinline__ float local_pos(unsigned long long x, unsigned long long O) {
   return fix_to_float(static_cast<long long>(x - O));
 }
+
+#ifndef DRR_JAC_UNROLL
+#define DRR_JAC_UNROLL 6
+#endif
+// Jacobian walk unroll: a multiple of 3, so that the three voxel registers of
+// its two-deep gather pipeline rotate without register moves.
+constexpr int kJacUnroll = DRR_JAC_UNROLL;
+#ifndef DRR_JAC_CHUNK
+#define DRR_JAC_CHUNK 31
+#endif
+// Jacobian chunk length: the first crossing of a chunk is peeled, so the
+// unrolled loop runs kJacChunk - 1 = 30 times, a whole number of unrolled bodies.
+constexpr int kJacChunk = DRR_JAC_CHUNK;
 
 template <int DT>
 __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetup& r, WalkScratch* ws) {
@@ -481,7 +500,7 @@ constexpr float kTieRel = 4.76837158203125e-7f;  // 2^-21 > twice 1.5 * 2^-23
 constexpr float kTieAbs = 4.f;                   // high-word units
 
 template <int DT>
-__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, WalkScratch* ws,
+__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, JacScratch* ws,
                                               JacSums& out) {
   const int t = threadIdx.x;
   int dom = 0;
@@ -490,7 +509,7 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
   const int a0 = dom == 0 ? 1 : 0;  // real axis of slot 0
   const int a1 = dom == 2 ? 1 : 2;  // real axis of slot 1
   const int ax_of[3] = {a0, a1, dom};
-  int step[3], cnt[3];
+  int step[3];
   float dl[3];
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
@@ -499,22 +518,22 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     ws->A0[sl][t] = pick3(a, r.A0[0], r.A0[1], r.A0[2]);
     ws->D[sl][t] = D;
     step[sl] = pick3(a, r.step[0], r.step[1], r.step[2]);
-    cnt[sl] = pick3(a, r.cnt[0], r.cnt[1], r.cnt[2]);
+    ws->cnt[sl][t] = pick3(a, r.cnt[0], r.cnt[1], r.cnt[2]);
     dl[sl] = fix_to_float(static_cast<long long>(D));
   }
   unsigned int k0 = 0u, k1 = 0u, k2 = 0u;  // crossings taken per slot before this chunk
-  unsigned long long O = 0ull;              // exact position of the chunk's anchor
+  unsigned long long O = 0ull;              // exact position of the last crossing taken (the anchor)
   int off = r.off;
-  float v = Voxel<DT>::load(vd.data, off);
-  float vprev = 0.f;
+  float v = Voxel<DT>::load(vd.data, off);  // voxel after the pending crossing
+  float vprev = 0.f;                        // voxel before it
   float F = 0.f, G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
-  // slot of the crossing that starts the current segment (neither: slot 2 or a clamped entry)
+  // slot of the pending crossing, the last one taken, whose weight is not yet
+  // summed (neither: slot 2 or a clamped entry); it sits at the anchor
   bool p0 = r.ea == a0, p1 = r.ea == a1;
   if (r.ea < 0) Gc = -v;  // entry clamped at alpha 0: weight -V_first
-  float last = 0.f;       // absolute position of the last crossing taken
   int remaining = r.nseg - 1;
-  for (;;) {
-    const int n = min(remaining, kChunk);
+  while (remaining > 0) {
+    const int n = min(remaining, kJacChunk);
     ws->c_off[t] = off;
     ws->c_v[t] = v;
     ws->c_vprev[t] = vprev;
@@ -524,43 +543,72 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], k2), O);
     float tx = x0, ty = y0, tz = z0;
     float lx = 0.f, ly = 0.f, lz = 0.f;
-    // chunk sums in local positions; the pending crossing sits at the anchor (0)
+    // chunk sums in local positions
     float ac = 0.f, f = 0.f, g0 = 0.f, g1 = 0.f, h0 = 0.f, h1 = 0.f;
+#define DRR_JAC_STEP(an, bx, by)                           \
+  const float an = fminf(fminf(tx, ty), tz);               \
+  const bool bx = tx == an;                                \
+  const bool by = !bx && ty == an;                         \
+  {                                                        \
+    const bool bz = !bx && !by;                            \
+    off += bx ? step[0] : (by ? step[1] : step[2]);        \
+    if (bx) lx += 1.f;                                     \
+    if (by) ly += 1.f;                                     \
+    if (bz) lz += 1.f;                                     \
+    tx = fmaf(lx, dl[0], x0);                              \
+    ty = fmaf(ly, dl[1], y0);                              \
+    tz = fmaf(lz, dl[2], z0);                              \
+  }
+#define DRR_JAC_ACCOUNT()                                  \
+  {                                                        \
+    const float wgt = vprev - v;                           \
+    if (p0) { g0 += wgt; h0 = fmaf(wgt, ac, h0); }         \
+    if (p1) { g1 += wgt; h1 = fmaf(wgt, ac, h1); }         \
+  }
+    // The gathers run two crossings ahead: crossing m+1 (an1, q0/q1, voxel v1
+    // after it) is taken while segment m is summed.
+    DRR_JAC_STEP(a1st, b1x, b1y)
+    float an1 = a1st;
+    bool q0 = b1x, q1 = b1y;
+    float v1 = Voxel<DT>::load(vd.data, off);
     float gmin = 3.0e38f;
-#pragma unroll kUnroll
-    for (int m = 0; m < n; ++m) {
-      {  // the crossing that started the current segment (its voxel is known by now)
-        const float wgt = vprev - v;
-        if (p0) { g0 += wgt; h0 = fmaf(wgt, ac, h0); }
-        if (p1) { g1 += wgt; h1 = fmaf(wgt, ac, h1); }
-      }
-      const float an = fminf(fminf(tx, ty), tz);
-      const bool bx = tx == an;
-      const bool by = !bx && ty == an;
-      const bool bz = !bx && !by;
-      off += bx ? step[0] : (by ? step[1] : step[2]);
-      if (bx) lx += 1.f;
-      if (by) ly += 1.f;
-      if (bz) lz += 1.f;
-      tx = fmaf(lx, dl[0], x0);
-      ty = fmaf(ly, dl[1], y0);
-      tz = fmaf(lz, dl[2], z0);
-      const float vn = Voxel<DT>::load(vd.data, off);
-      const float seg = an - ac;
+#pragma unroll kJacUnroll
+    for (int m = 1; m < n; ++m) {
+      DRR_JAC_ACCOUNT()
+      DRR_JAC_STEP(an2, bx, by)
+      const float v2 = Voxel<DT>::load(vd.data, off);
+      const float seg = an1 - ac;
       gmin = fminf(gmin, seg);
       f = fmaf(seg, v, f);
-      ac = an;
-      p0 = bx;
-      p1 = by;
+      ac = an1;
+      p0 = q0;
+      p1 = q1;
+      q0 = bx;
+      q1 = by;
       vprev = v;
-      v = vn;
+      v = v1;
+      v1 = v2;
+      an1 = an2;
     }
+    // drain: the segment that ends at the chunk's last crossing
+    DRR_JAC_ACCOUNT()
+    {
+      const float seg = an1 - ac;
+      gmin = fminf(gmin, seg);
+      f = fmaf(seg, v, f);
+    }
+    ac = an1;
+    p0 = q0;
+    p1 = q1;
+    vprev = v;
+    v = v1;
     unsigned int c0 = static_cast<unsigned int>(lx), c1 = static_cast<unsigned int>(ly),
                  c2 = static_cast<unsigned int>(lz);
+    // The float order is exact unless two crossings came within the FP32 error
+    // of the local positions: check the chunk's shortest segment and the gap to
+    // the next crossing after it.
     const float next = fminf(fminf(tx, ty), tz);
-    const bool tie = gmin < fmaf(ac, kTieRel, kTieAbs) ||
-                     (remaining > n && next - ac < fmaf(next, kTieRel, kTieAbs));
-    if (tie) {
+    if (gmin < fmaf(ac, kTieRel, kTieAbs) || (remaining > n && next - ac < fmaf(next, kTieRel, kTieAbs))) {
       // exact re-walk of the chunk: candidates compared as 64-bit fixed point
       off = ws->c_off[t];
       v = ws->c_v[t];
@@ -571,15 +619,13 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
       ac = f = g0 = g1 = h0 = h1 = 0.f;
       c0 = c1 = c2 = 0u;
       for (int m = 0; m < n; ++m) {
-        const float wgt = vprev - v;
-        if (p0) { g0 += wgt; h0 = fmaf(wgt, ac, h0); }
-        if (p1) { g1 += wgt; h1 = fmaf(wgt, ac, h1); }
+        DRR_JAC_ACCOUNT()
         const unsigned int kk[3] = {k0 + c0, k1 + c1, k2 + c2};
         unsigned long long best = ~0ull;
         int sel = 2;
 #pragma unroll
         for (int sl = 0; sl < 3; ++sl) {
-          if (static_cast<int>(kk[sl]) < cnt[sl]) {
+          if (static_cast<int>(kk[sl]) < ws->cnt[sl][t]) {
             const unsigned long long e = fix_at(ws->A0[sl][t], ws->D[sl][t], kk[sl]);
             if (e < best) { best = e; sel = sl; }
           }
@@ -599,31 +645,33 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
         v = vn;
       }
     }
+#undef DRR_JAC_STEP
+#undef DRR_JAC_ACCOUNT
     remaining -= n;
     k0 += c0;
     k1 += c1;
     k2 += c2;
-    // chunk sums to the anchor frame: alpha = O + local
-    const float Of = fix_to_float(static_cast<long long>(O));
-    G0 += g0;
-    A0 += fmaf(Of, g0, h0);
-    G1 += g1;
-    A1 += fmaf(Of, g1, h1);
-    if (remaining == 0) {
-      F += fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O) - ac, v, f);
-      last = Of + ac;
-      break;
-    }
-    // the last crossing taken (the largest one) is the next anchor; the float
-    // position used for it in f is corrected to the exact one
+    // the chunk's last crossing (the largest one taken) is the next anchor; the
+    // segment that ends there gets its exact end
     unsigned long long Onew = O;
     if (k0) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], k0 - 1u));
     if (k1) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], k1 - 1u));
     if (k2) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], k2 - 1u));
-    F += fmaf(local_pos(Onew, O) - ac, v, f);
+    f = fmaf(local_pos(Onew, O) - ac, vprev, f);
+    // chunk sums to absolute positions: alpha = O + local
+    const float Of = fix_to_float(static_cast<long long>(O));
+    F += f;
+    G0 += g0;
+    A0 += fmaf(Of, g0, h0);
+    G1 += g1;
+    A1 += fmaf(Of, g1, h1);
     O = Onew;
   }
-  {  // the last crossing taken
+  // the last segment, from the last crossing (the anchor) to the exit, and the
+  // last crossing's weight at its absolute position
+  F = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O), v, F);
+  {
+    const float last = fix_to_float(static_cast<long long>(O));
     const float wgt = vprev - v;
     if (p0) { G0 += wgt; A0 = fmaf(wgt, last, A0); }
     if (p1) { G1 += wgt; A1 = fmaf(wgt, last, A1); }
@@ -634,12 +682,12 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
   if (r.xa < 0) { Gc += v; Ac = v * ex; }
   else if (r.xa == a0) { G0 += v; A0 = fmaf(v, ex, A0); }
   else if (r.xa == a1) { G1 += v; A1 = fmaf(v, ex, A1); }
-  // back to alpha units
+  // back to alpha units and real axes (static indices)
   const float u = r.unit;
   out.F = F * u;
   out.dom = dom;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {  // back to real axes (static indices)
+  for (int a = 0; a < 3; ++a) {
     out.G[a] = a == a0 ? G0 : (a == a1 ? G1 : -(G0 + G1 + Gc));  // sum of all crossing weights is 0
     out.A[a] = a == a0 ? A0 * u : (a == a1 ? A1 * u : 0.f);      // the dominant axis is handled through R
   }
@@ -732,6 +780,19 @@ __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RayS
     atomicAdd(gvol + lin, s * static_cast<float>(static_cast<int>(kExitUnits - ac)));
 }
 
+template <int MODE>
+struct ScratchFor {
+  using type = WalkScratch;
+};
+template <>
+struct ScratchFor<kFwdJac> {
+  using type = JacScratch;
+};
+template <>
+struct ScratchFor<kPoseGrad> {
+  using type = JacScratch;
+};
+
 template <int MODE, int DT>
 __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gscale,
                                           float* __restrict__ gvol, WalkScratch* ws, RayResult& res) {
@@ -755,7 +816,7 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
     res.F = walk_forward<DT>(vd, r, ws) * L * vd.out_scale;
   } else if (MODE == kFwdJac || MODE == kPoseGrad) {
     JacSums s;
-    walk_jacobian<DT>(vd, r, ws, s);
+    walk_jacobian<DT>(vd, r, static_cast<JacScratch*>(ws), s);
     res.F = s.F * L * vd.out_scale;
     pose_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
   } else if (MODE == kBackproject) {
@@ -771,7 +832,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
                                                           float* __restrict__ partials, float* __restrict__ gvol) {
   __shared__ PoseGeom spg;
   __shared__ float red[kThreads / 32][6];
-  __shared__ WalkScratch ws;
+  __shared__ typename ScratchFor<MODE>::type ws;
   const int b = blockIdx.z;
   {
     const unsigned int* src = reinterpret_cast<const unsigned int*>(pgs + b);
@@ -945,7 +1006,7 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
   __shared__ PoseGeom spg;
   __shared__ ServeRequest sr;
   __shared__ float red[kThreads / 32][6];
-  __shared__ WalkScratch ws;
+  __shared__ JacScratch ws;
   __shared__ int s_tile;
   const int nreq = hdr->nreq, total = hdr->total_tiles;
   for (;;) {
