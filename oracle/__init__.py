@@ -74,7 +74,7 @@ def _load():
         lib.oracle_sample_ray.restype = ctypes.c_double
         lib.oracle_render.argtypes = [_ip, _dp, _fp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32, _i64p,
-                                      ctypes.c_int64, _dp, _dp, ctypes.c_int32]
+                                      ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int32]
         lib.oracle_render.restype = ctypes.c_int
         lib.oracle_pose_grad.argtypes = [_ip, _dp, _fp, ctypes.c_double, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_double, ctypes.c_double, _fp,
@@ -181,11 +181,13 @@ def sample_ray(vol: Volume, s, p, nsamples: int):
                                  int(nsamples))
 
 
-def render(vol: Volume, det, poses, pixels=None, jacobian: bool = False, threads: int = 0):
+def render(vol: Volume, det, poses, pixels=None, jacobian: bool = False, threads: int = 0,
+           geometry: bool = False):
     """DRR for every pose: (B, H, W) float64, or (B, len(pixels)) for a flat pixel list.
 
     det = (sdr, H, W, dh, dw).  With jacobian=True also returns dE/d(rz,ry,rx,tx,ty,tz)
-    per ray: (B, H, W, 6) or (B, npix, 6).
+    per ray: (B, H, W, 6) or (B, npix, 6); with geometry=True (after it) dE/d(sdr, dh, dw)
+    per ray: (B, H, W, 3) or (B, npix, 3).
     """
     lib = _load()
     sdr, H, W, dh, dw = det
@@ -200,14 +202,26 @@ def render(vol: Volume, det, poses, pixels=None, jacobian: bool = False, threads
         pix_ptr = _ptr(pixels, ctypes.c_int64)
     out = np.zeros((B, npix))
     jac = np.zeros((B, npix, 6)) if jacobian else None
+    geo = np.zeros((B, npix, 3)) if geometry else None
     lib.oracle_render(*vol._args(), float(sdr), int(H), int(W), float(dh), float(dw),
                       _ptr(poses, ctypes.c_float), int(B), pix_ptr, int(npix), _ptr(out, ctypes.c_double),
-                      _ptr(jac, ctypes.c_double) if jacobian else None, int(threads))
+                      _ptr(jac, ctypes.c_double) if jacobian else None,
+                      _ptr(geo, ctypes.c_double) if geometry else None, int(threads))
     if pixels is None:
         out = out.reshape(B, H, W)
         if jacobian:
             jac = jac.reshape(B, H, W, 6)
-    return (out, jac) if jacobian else out
+        if geometry:
+            geo = geo.reshape(B, H, W, 3)
+    res = (out,) + ((jac,) if jacobian else ()) + ((geo,) if geometry else ())
+    return res if len(res) > 1 else out
+
+
+def geometry_grad(vol: Volume, det, poses, grad_out, threads: int = 0):
+    """dL/d(sdr, dh, dw) per pose: sum over pixels of grad_out * dE/d(sdr, dh, dw), (B, 3)."""
+    _, geo = render(vol, det, poses, geometry=True, threads=threads)
+    g = np.asarray(grad_out, np.float64).reshape(geo.shape[:-1])
+    return np.einsum("bhw,bhwk->bk", g, geo)
 
 
 def pose_grad(vol: Volume, det, poses, grad_out, threads: int = 0):
@@ -315,6 +329,15 @@ def zncc_loss(moving, fixed, eps: float = 1e-8):
     Ih = Ic / (np.sqrt((Ic ** 2).mean(axis=1, keepdims=True)) + eps)
     Fh = Fc / (np.sqrt((Fc ** 2).mean(axis=1, keepdims=True)) + eps)
     return -(Ih * Fh).mean(axis=1)
+
+
+def loss_landscape(vol: Volume, det, fixed, poses, eps: float = 1e-8, threads: int = 0):
+    """-ZNCC between the DRR at each pose and one fixed image (the loss-landscape study,
+    Sec. 3.2): render every pose (Eq. 2), then zncc_loss against the same fixed image."""
+    poses = np.asarray(poses, np.float32).reshape(-1, 6)
+    E = render(vol, det, poses, threads=threads)
+    F = np.broadcast_to(np.asarray(fixed, np.float64), E.shape)
+    return zncc_loss(E, F, eps)
 
 
 def zncc_loss_grad(moving, fixed, eps: float = 1e-8):

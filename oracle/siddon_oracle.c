@@ -319,10 +319,15 @@ double oracle_sample_ray(const int32_t n[3], const double delta[3], const float*
 /*
  * out[b][q] = E for pose b and pixel pix[q] (flat h*W + w); pix == NULL means
  * every pixel (npix = H*W).  jac (optional) [b][q][6] = dE/d(rz, ry, rx, tx, ty, tz).
+ * geo (optional) [b][q][3] = dE/d(sdr, dh, dw), the detector parameters (Sec. 3.2
+ * notes the generator also differentiates with respect to the source-to-detector
+ * distance 2 rho and the pixel spacing): with s = R (rho,0,0) + t, rho = sdr/2, and
+ * p = R (-rho, (w-(W-1)/2) dw, (h-(H-1)/2) dh) + t, by the chain rule through s and p.
  */
 int oracle_render(const int32_t n[3], const double delta[3], const float* vol, double sdr,
                   int32_t H, int32_t W, double dh, double dw, const float* poses, int32_t B,
-                  const int64_t* pix, int64_t npix, double* out, double* jac, int32_t nthreads) {
+                  const int64_t* pix, int64_t npix, double* out, double* jac, double* geo,
+                  int32_t nthreads) {
   if (!pix) npix = (int64_t)H * W;
   int64_t total = (int64_t)B * npix;
 #ifdef _OPENMP
@@ -351,9 +356,27 @@ int oracle_render(const int32_t n[3], const double delta[3], const float* vol, d
         p[a] += pose[3 + a];
       }
       double gs[3], gp[3];
-      double E = siddon_ray(n, delta, vol, s, p, jac ? gs : NULL, jac ? gp : NULL, list, NULL,
+      const int want = jac || geo;
+      double E = siddon_ray(n, delta, vol, s, p, want ? gs : NULL, want ? gp : NULL, list, NULL,
                             NULL);
       out[r] = E;
+      if (geo) {
+        /* ds/dsdr = R (1/2, 0, 0); dp/dsdr = R (-1/2, 0, 0); dp/ddh = R (0, 0, h-(H-1)/2);
+           dp/ddw = R (0, w-(W-1)/2, 0) */
+        const double e_sdr_s[3] = {0.5, 0.0, 0.0}, e_sdr_p[3] = {-0.5, 0.0, 0.0};
+        const double e_dh[3] = {0.0, 0.0, (double)h - 0.5 * (double)(H - 1)};
+        const double e_dw[3] = {0.0, (double)w - 0.5 * (double)(W - 1), 0.0};
+        double vs[3], vp[3], vh[3], vw[3];
+        mat3_vec(R, e_sdr_s, vs);
+        mat3_vec(R, e_sdr_p, vp);
+        mat3_vec(R, e_dh, vh);
+        mat3_vec(R, e_dw, vw);
+        double* G = geo + 3 * r;
+        G[0] = gs[0] * vs[0] + gs[1] * vs[1] + gs[2] * vs[2] + gp[0] * vp[0] + gp[1] * vp[1] +
+               gp[2] * vp[2];
+        G[1] = gp[0] * vh[0] + gp[1] * vh[1] + gp[2] * vh[2];
+        G[2] = gp[0] * vw[0] + gp[1] * vw[1] + gp[2] * vw[2];
+      }
       if (jac) {
         double* J = jac + 6 * r;
         for (int j = 0; j < 3; ++j) {
@@ -383,7 +406,7 @@ int oracle_pose_grad(const int32_t n[3], const double delta[3], const float* vol
     free(J);
     return 1;
   }
-  oracle_render(n, delta, vol, sdr, H, W, dh, dw, poses, B, NULL, npix, E, J, nthreads);
+  oracle_render(n, delta, vol, sdr, H, W, dh, dw, poses, B, NULL, npix, E, J, NULL, nthreads);
   for (int32_t b = 0; b < B; ++b)
     for (int k = 0; k < 6; ++k) {
       double acc = 0.0;

@@ -164,6 +164,18 @@ def pose_offsets(batch: int, seed: int, max_angle_deg: float = 15.0, max_trans_m
     return random_poses(batch, seed, max_angle_deg, max_trans_mm)
 
 
+def landscape_offsets(n: int, seed: int, rot_range_deg=(90.0, 90.0, 45.0),
+                      trans_range_mm=(30.0, 30.0, 30.0)) -> np.ndarray:
+    """(n, 6) float32 pose displacements for a loss-landscape sweep: each parameter
+    uniform on an interval of the given width centred on zero.  The defaults are the
+    widths of the paper's landscape study (Sec. 3.2): 90 deg for the two source
+    angles (rz, ry here), 45 deg for the roll (rx), 30 mm per translation."""
+    rng = np.random.default_rng(seed)
+    half = np.concatenate([np.deg2rad(np.asarray(rot_range_deg, np.float64)),
+                           np.asarray(trans_range_mm, np.float64)]) / 2.0
+    return rng.uniform(-half, half, size=(n, 6)).astype(np.float32)
+
+
 def upstream_grad(shape, seed: int) -> np.ndarray:
     """Seeded upstream gradient dL/dDRR ~ U(-1, 1), float32."""
     rng = np.random.default_rng(seed)
@@ -190,6 +202,12 @@ REGISTRATION = dict(  # same CT, 256x256 detector, 64 concurrent registrations
     name="registration_512x512x133_256x256_b64",
     shape_zyx=(133, 512, 512), spacing=(0.703, 0.703, 2.5),
     detector=Detector(510.0, 256, 256, 1.4, 1.4), batch=64, truth_seed=4, offset_seed=5, steps=200,
+)
+
+LANDSCAPE = dict(  # same CT, 200x200 detector: -ZNCC at 4096 displacements around one pose
+    name="landscape_512x512x133_200x200_n4096",
+    shape_zyx=(133, 512, 512), spacing=(0.703, 0.703, 2.5),
+    detector=Detector(510.0, 200, 200, 1.4, 1.4), n=4096, truth_seed=9, offset_seed=10,
 )
 
 PRECISION = dict(  # 512^3 at 0.5 mm, 1024x1024 detector, 8 poses
