@@ -339,6 +339,37 @@ def registration_bench(drr, hu, lr_rot=1e-2, lr_trans=1.0):
             "workload": "512x512x133 CT, 256x256 @1.4 mm, SDR 510; 64 problems, offsets U(+-15 deg, +-20 mm)"}
 
 
+def landscape_bench(drr, hu, reps=3):
+    """The loss-landscape workload (Sec. 3.2): -ZNCC of 4096 DRRs (200x200) of the CT at
+    displacements U(90, 90, 45 deg; 30 mm widths) around one pose against the DRR at that pose."""
+    import torch
+    from paper_2208_12737_gb300 import inputs
+    cfg = inputs.LANDSCAPE
+    vol = drr.Volume(hu, cfg["spacing"], hu=True)
+    det = cfg["detector"]
+    truth = inputs.random_poses(1, seed=cfg["truth_seed"])
+    poses = torch.from_numpy((truth + inputs.landscape_offsets(cfg["n"], seed=cfg["offset_seed"])).astype(np.float32))
+    poses = poses.cuda()
+    fixed = drr.render(vol, det, torch.from_numpy(truth).cuda())[0]
+    out = torch.empty((cfg["n"],), device="cuda")
+    drr.loss_landscape(vol, det, fixed, poses, out=out)  # warm-up
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        drr.loss_landscape(vol, det, fixed, poses, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    L = out.cpu().numpy()
+    rays = cfg["n"] * det.height * det.width
+    return {"poses": cfg["n"], "ms": t, "drrs_per_s": cfg["n"] / (t * 1e-3), "grays_per_s": rays / (t * 1e-3) / 1e9,
+            "loss_min": float(L.min()), "loss_median": float(np.median(L)),
+            "workload": "512x512x133 CT, 200x200 @1.4 mm, SDR 510; 4096 displacements U(90,90,45 deg; 30 mm)"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -469,6 +500,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_registration:
         line["registration"] = registration_bench(drr, hu)
+    if not args.no_landscape:
+        line["landscape"] = landscape_bench(drr, hu)
     if not args.no_serve:
         line["served"] = serve_bench(drr, hu, seconds=args.serve_seconds)
         line["served_p50_ms"] = line["served"]["p50_ms"]
@@ -492,6 +525,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-registration", action="store_true")
+    ap.add_argument("--no-landscape", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

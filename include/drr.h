@@ -191,6 +191,34 @@ drr_status drr_adam_step(float* params_dev, const float* grads_dev, float* m_dev
                          int32_t step, float lr_rot, float lr_trans, float beta1, float beta2, float eps,
                          void* cuda_stream);
 
+/* Gradient with respect to the detector parameters (Sec. 3.2 notes that the
+ * generator also differentiates with respect to the source-to-detector
+ * distance 2 rho and the pixel spacing; Sec. 2.4 gives s = R (rho,0,0) + t and
+ * p = R (-rho, (w-(W-1)/2) dw, (h-(H-1)/2) dh) + t with rho = sdr/2):
+ *  grad_drr_dev      : [B][H][W] float32, device, dL/dE;
+ *  grad_geometry_dev : [B][3] float32, device, overwritten with
+ *                      sum over pixels of dL/dE * dE/d(sdr_mm, delta_h_mm, delta_w_mm)
+ *                      for each pose (sum over B for a detector shared by all poses).
+ * A re-walk with the fused per-ray Jacobian (same arithmetic as drr_render with
+ * a Jacobian), reduced per 8x4-pixel tile and then in FP64 in a fixed order.
+ * Asynchronous on cuda_stream.  Errors: DRR_ERR_INVALID, DRR_ERR_CUDA. */
+drr_status drr_geometry_grad(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
+                             const float* grad_drr_dev, float* grad_geometry_dev, void* cuda_stream);
+
+/* Loss landscape (Sec. 3.2, the study of the negative-ZNCC landscape around the
+ * true pose): loss_out[i] = -ZNCC(E(pose_i), fixed) for N poses and one fixed
+ * image, with the statistics of drr_zncc (population, FP64, eps).
+ *  fixed_dev    : [H][W] float32, device;
+ *  poses_dev    : [N][6] float32, device (e.g. a grid of displacements around a pose);
+ *  loss_out_dev : [N] float32, device, overwritten;
+ *  chunk        : poses rendered per pass (0: as many as fit in 256 MB of DRRs,
+ *                 at most 4096); the DRR scratch is allocated from the device's
+ *                 stream-ordered pool and released on the stream.
+ * Asynchronous on cuda_stream.  Errors: DRR_ERR_INVALID (bad sizes, NULL
+ * pointers, eps < 0), DRR_ERR_CUDA. */
+drr_status drr_loss_landscape(drr_volume v, const drr_detector* det, const float* fixed_dev, const float* poses_dev,
+                              int32_t N, float eps, float* loss_out_dev, int32_t chunk, void* cuda_stream);
+
 /* ---- serving: continuous batching of render / render+gradient requests ---- */
 /* No counterpart in the paper (whose method is a library call); this is the
  * request loop of the serving workload.  A host thread forms "ticks": it admits

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -118,11 +119,12 @@ struct AsyncBuf {
 
 // ---- kernel timing: CUDA events around each launch while enabled ----------
 enum ProfKernel {
-  kPoseSetup, kSiddonFwd, kSiddonFwdJac, kSiddonPoseGrad, kJacReduce, kFinalize, kBackproject, kCountSeg, kNumProf
+  kPoseSetup, kSiddonFwd, kSiddonFwdJac, kSiddonPoseGrad, kJacReduce, kFinalize, kBackproject, kCountSeg, kZncc,
+  kSiddonGeoGrad, kNumProf
 };
 const char* const kProfNames[kNumProf] = {"pose_setup",        "siddon_fwd", "siddon_fwd_jac",     "siddon_pose_grad",
                                           "jac_reduce",        "pose_grad_finalize", "siddon_backproject",
-                                          "count_segments"};
+                                          "count_segments",    "zncc",       "siddon_geometry_grad"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -179,7 +181,11 @@ namespace {
 
 drr_status setup_geometry(drr_volume v, const drr::DetDev& dd, const float* poses_dev, int32_t B, cudaStream_t st,
                           AsyncBuf<drr::PoseGeom>& pg) {
-  DRR_CUDA(pg.alloc(size_t(B), st), "cudaMallocAsync(pose geometry)");
+  // one PoseGeom per pose plus one slot for the walk kernels' tile counters
+  static_assert(sizeof(drr::PoseGeom) >= drr::kLaunchCounters * sizeof(unsigned int), "counter slot");
+  if (int64_t(drr::pose_tiles(dd)) * B >= (int64_t{1} << 31))
+    return drr::set_error(DRR_ERR_INVALID, "too many rays in one call (B * pixels / 32 must stay below 2^31)");
+  DRR_CUDA(pg.alloc(size_t(B) + 1, st), "cudaMallocAsync(pose geometry)");
   LaunchScope ls(kPoseSetup, st);
   DRR_CUDA(drr::launch_pose_setup(poses_dev, B, dd, &v->vd, pg.p, st), "pose_setup launch");
   return DRR_OK;
@@ -454,6 +460,59 @@ drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float
   if (drr_status s = setup_geometry(v, dd, poses_dev, B, st, pg)) return s;
   LaunchScope ls(kCountSeg, st);
   DRR_CUDA(drr::launch_count_segments(v->vd, dd, pg.p, B, segments_out_dev, st), "count_segments launch");
+  return DRR_OK;
+}
+
+drr_status drr_geometry_grad(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
+                             const float* grad_drr_dev, float* grad_geometry_dev, void* cuda_stream) {
+  if (drr_status s = check_volume(v)) return s;
+  drr::DetDev dd;
+  if (drr_status s = check_detector(det, &dd)) return s;
+  if (drr_status s = check_geometry(v->vd, dd)) return s;
+  if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
+  if (!poses_dev || !grad_drr_dev || !grad_geometry_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  configure_pool(v->device);
+  AsyncBuf<drr::PoseGeom> pg;
+  if (drr_status s = setup_geometry(v, dd, poses_dev, B, st, pg)) return s;
+  AsyncBuf<float> partials;
+  DRR_CUDA(partials.alloc(size_t(B) * drr::pose_tiles(dd) * 3, st), "cudaMallocAsync(geometry-gradient partials)");
+  LaunchScope ls(kSiddonGeoGrad, st);
+  DRR_CUDA(drr::launch_geometry_grad(v->vd, dd, pg.p, B, grad_drr_dev, partials.p, grad_geometry_dev, st),
+           "geometry-gradient launch");
+  drr::count_launches(1);  // the finalize launch
+  return DRR_OK;
+}
+
+drr_status drr_loss_landscape(drr_volume v, const drr_detector* det, const float* fixed_dev, const float* poses_dev,
+                              int32_t N, float eps, float* loss_out_dev, int32_t chunk, void* cuda_stream) {
+  if (drr_status s = check_volume(v)) return s;
+  drr::DetDev dd;
+  if (drr_status s = check_detector(det, &dd)) return s;
+  if (drr_status s = check_geometry(v->vd, dd)) return s;
+  if (N <= 0) return drr::set_error(DRR_ERR_INVALID, "N must be positive");
+  if (chunk < 0) return drr::set_error(DRR_ERR_INVALID, "chunk must be >= 0");
+  if (!(eps >= 0.f)) return drr::set_error(DRR_ERR_INVALID, "eps must be >= 0");
+  if (!fixed_dev || !poses_dev || !loss_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  const int64_t npix = int64_t(dd.H) * dd.W;
+  if (chunk == 0) chunk = int32_t(std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t{256} << 20) / (4 * npix))));
+  chunk = std::min(chunk, std::min<int32_t>(N, 65535));
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  configure_pool(v->device);
+  AsyncBuf<float> E;
+  DRR_CUDA(E.alloc(size_t(chunk) * npix, st), "cudaMallocAsync(landscape DRRs)");
+  for (int32_t i = 0; i < N; i += chunk) {
+    const int32_t c = std::min(chunk, N - i);
+    AsyncBuf<drr::PoseGeom> pg;
+    if (drr_status s = setup_geometry(v, dd, poses_dev + 6 * size_t(i), c, st, pg)) return s;
+    {
+      LaunchScope ls(kSiddonFwd, st);
+      DRR_CUDA(drr::launch_render(v->vd, dd, pg.p, c, E.p, nullptr, st), "landscape render launch");
+    }
+    LaunchScope ls(kZncc, st);
+    DRR_CUDA(drr::launch_zncc(E.p, fixed_dev, 0, c, int(npix), eps, loss_out_dev + i, nullptr, st),
+             "landscape zncc launch");
+  }
   return DRR_OK;
 }
 

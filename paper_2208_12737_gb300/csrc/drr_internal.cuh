@@ -26,6 +26,10 @@ constexpr int kWarpsX = kTileW / kWarpTileW;
 static_assert(kWarpTileW >= 4 && kWarpTileW <= 32 && 32 % kWarpTileW == 0, "warp tile width");
 static_assert((kTileW / kWarpTileW) * (kTileH / kWarpTileH) == kThreads / 32, "8 warps per block tile");
 
+// Tile counters of the walk kernels, kept in the geometry buffer right after the
+// last pose's PoseGeom and zeroed by the pose-setup kernel.
+constexpr int kLaunchCounters = 4;
+
 // Pixel of thread `tid` in block tile (tx, ty).
 __host__ __device__ __forceinline__ void tile_pixel(int tx, int ty, int tid, int* h, int* w) {
   const int lane = tid & 31, warp = tid >> 5;
@@ -51,6 +55,10 @@ struct PoseGeom {
   float Q[3][3];   // dR/d eta_j * (p_c(0,0) - s_c)
   float Wv[3][3];  // dR/d eta_j * (0, dw, 0)
   float Hv[3][3];  // dR/d eta_j * (0, 0, dh)
+  // Chain-rule terms for the detector parameters: the columns of R (R e_x,
+  // R e_y, R e_z), and the detector centre indices (H-1)/2, (W-1)/2.
+  float Rc[3][3];
+  float hc, wc;
 };
 
 // A device-resident volume as the kernels see it.
@@ -69,6 +77,11 @@ struct DetDev {
   int H, W;
   float sdr, dh, dw;
 };
+
+// Warp tiles (kWarpTileW x kWarpTileH pixels) per pose: the work units of the walk kernels.
+__host__ __device__ __forceinline__ int pose_tiles(const DetDev& det) {
+  return ((det.W + kWarpTileW - 1) / kWarpTileW) * ((det.H + kWarpTileH - 1) / kWarpTileH);
+}
 
 // One admitted request as the serving kernels see it (device-resident table).
 struct ServeRequest {
@@ -101,11 +114,19 @@ cudaError_t launch_ray_setup(const float* poses, int B, const DetDev& det, float
 cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
                           cudaStream_t stream);
 // Pose gradient by re-tracing (jac == nullptr) or from a stored Jacobian.
+// Negative ZNCC of B moving images against fixed images fixed_stride elements
+// apart (0: one fixed image for all), and optionally d loss / d moving.
+cudaError_t launch_zncc(const float* moving, const float* fixed, size_t fixed_stride, int B, int npix, float eps,
+                        float* loss, float* grad, cudaStream_t stream);
 // partials must hold B * pose_grad_blocks(det) * 6 floats.
 int pose_grad_blocks(const DetDev& det, bool from_jacobian);
 cudaError_t launch_pose_grad_partials(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
                                       const float* grad_drr, const float* jac, float* partials, cudaStream_t stream);
 cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream);
+// dL/d(sdr, dh, dw) per pose by a re-walk: partials must hold
+// B * pose_tiles(det) * 3 floats; grad_geometry is [B][3].
+cudaError_t launch_geometry_grad(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
+                                 const float* grad_drr, float* partials, float* grad_geometry, cudaStream_t stream);
 // The stored-Jacobian half of launch_pose_grad_partials on its own.
 cudaError_t launch_jac_reduce(const DetDev& det, int B, const float* grad_drr, const float* jac, float* partials,
                               cudaStream_t stream);

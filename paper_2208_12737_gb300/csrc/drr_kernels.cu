@@ -9,6 +9,8 @@
 //            each axis' next plane, iterated until the ray leaves the volume
 //   Sec. 2.3 entry/exit clip a_min / a_max
 //   Sec. 2.4 pose parameterisation and differentiation w.r.t. the pose
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -17,7 +19,7 @@
 namespace drr {
 namespace {
 
-enum Mode : int { kFwd = 0, kFwdJac = 1, kPoseGrad = 2, kBackproject = 3, kCount = 4 };
+enum Mode : int { kFwd = 0, kFwdJac = 1, kPoseGrad = 2, kBackproject = 3, kCount = 4, kGeoGrad = 5 };
 
 template <int DT>
 struct Voxel;
@@ -116,6 +118,16 @@ __device__ void compute_pose_geom(const float* pose, const DetDev& det, const Vo
     g.gw[a] = ew[a] / dl;
     g.gh[a] = eh[a] / dl;
   }
+  // R e_x = (s - t) / rho, R e_y = ew / dw, R e_z = eh / dh
+  const double rho = sc[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g.Rc[0][a] = static_cast<float>((s[a] - static_cast<double>(pose[3 + a])) / rho);
+    g.Rc[1][a] = static_cast<float>(ew[a] / static_cast<double>(det.dw));
+    g.Rc[2][a] = static_cast<float>(eh[a] / static_cast<double>(det.dh));
+  }
+  g.hc = 0.5f * static_cast<float>(det.H - 1);
+  g.wc = 0.5f * static_cast<float>(det.W - 1);
   const double q[3] = {pc00[0] - sc[0], pc00[1] - sc[1], pc00[2] - sc[2]};
   const double vw[3] = {0.0, static_cast<double>(det.dw), 0.0};
   const double vh[3] = {0.0, 0.0, static_cast<double>(det.dh)};
@@ -136,6 +148,8 @@ __device__ void compute_pose_geom(const float* pose, const DetDev& det, const Vo
 __global__ void pose_setup_kernel(const float* __restrict__ poses, int B, DetDev det, VolumeDev vd,
                                   PoseGeom* __restrict__ out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  // the walk kernels' tile counters live in the slot after the last pose
+  if (b < kLaunchCounters) reinterpret_cast<unsigned int*>(out + B)[b] = 0u;
   if (b >= B) return;
   PoseGeom g;
   compute_pose_geom(poses + 6 * b, det, vd, g);
@@ -349,7 +363,7 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 #define DRR_UNROLL 8
 #endif
 #ifndef DRR_FWD_MINB
-#define DRR_FWD_MINB 6
+#define DRR_FWD_MINB 5
 #endif
 #ifndef DRR_JAC_MINB
 #define DRR_JAC_MINB 4
@@ -704,14 +718,13 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
 //   dE/dp_a = (L R - F (L^2 - d_a^2) / L) / d_a,
 // which has no cancellation for rays nearly along that axis.
 //   dE/d eta_j = dE/dt . (dR_j s_c) + dE/dp . (dR_j (p_c - s_c)).
-__device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& s, const PoseGeom& pg, int h, int w,
-                                              float scale, float J[6]) {
-  const float L2 = r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2];
+// gt = dE/dt, gp = dE/dp in world units.
+__device__ __forceinline__ void ray_world_grads(const RaySetup& r, const JacSums& s, float gt[3], float gp[3]) {
+  const float L2 = fmaf(r.d[2], r.d[2], fmaf(r.d[1], r.d[1], r.d[0] * r.d[0]));
   const float L = sqrtf(L2);
   const float F = s.F;
   const float am = static_cast<float>(r.amin);
   float R = fmaf(am, s.Gc, s.Ac);
-  float gt[3], gp[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     if (a != s.dom) R += fmaf(am, s.G[a], s.A[a]);
@@ -734,6 +747,12 @@ __device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& 
       gp[a] = 0.f;
     }
   }
+}
+
+__device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& s, const PoseGeom& pg, int h, int w,
+                                              float scale, float J[6]) {
+  float gt[3], gp[3];
+  ray_world_grads(r, s, gt, gp);
   const float fw = static_cast<float>(w), fh = static_cast<float>(h);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -748,6 +767,28 @@ __device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& 
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) J[3 + a] = gt[a] * scale;
+}
+
+// dE/d(sdr, dh, dw) for one ray: the detector parameters (the paper notes the
+// generator also differentiates with respect to the source-to-detector
+// distance 2 rho and the pixel spacing, Sec. 3.2).  With s = R (rho,0,0) + t,
+// rho = sdr / 2, p = R (-rho, (w - wc) dw, (h - hc) dh) + t and dE/ds = gt - gp:
+//   dE/dsdr = (dE/ds - dE/dp) . R e_x / 2,
+//   dE/ddh  = (h - hc) dE/dp . R e_z,   dE/ddw = (w - wc) dE/dp . R e_y.
+__device__ __forceinline__ void geometry_jacobian(const RaySetup& r, const JacSums& s, const PoseGeom& pg, int h,
+                                                  int w, float scale, float J[3]) {
+  float gt[3], gp[3];
+  ray_world_grads(r, s, gt, gp);
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    a0 = fmaf(gt[a] - 2.f * gp[a], pg.Rc[0][a], a0);
+    a1 = fmaf(gp[a], pg.Rc[2][a], a1);
+    a2 = fmaf(gp[a], pg.Rc[1][a], a2);
+  }
+  J[0] = 0.5f * a0 * scale;
+  J[1] = (static_cast<float>(h) - pg.hc) * a1 * scale;
+  J[2] = (static_cast<float>(w) - pg.wc) * a2 * scale;
 }
 
 // Back-projection walk: grad_V[voxel] += g L (a_{m+1} - a_m), the transpose of
@@ -792,6 +833,10 @@ template <>
 struct ScratchFor<kPoseGrad> {
   using type = JacScratch;
 };
+template <>
+struct ScratchFor<kGeoGrad> {
+  using type = JacScratch;
+};
 
 template <int MODE, int DT>
 __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& pg, int h, int w, float gscale,
@@ -811,72 +856,97 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
   if (rs == 0) return;
   res.nseg = r.nseg;
   if (MODE == kCount) return;
-  const float L = sqrtf(r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2]);
+  const float L = sqrtf(fmaf(r.d[2], r.d[2], fmaf(r.d[1], r.d[1], r.d[0] * r.d[0])));
   if (MODE == kFwd) {
     res.F = walk_forward<DT>(vd, r, ws) * L * vd.out_scale;
-  } else if (MODE == kFwdJac || MODE == kPoseGrad) {
+  } else if (MODE == kFwdJac || MODE == kPoseGrad || MODE == kGeoGrad) {
     JacSums s;
     walk_jacobian<DT>(vd, r, static_cast<JacScratch*>(ws), s);
     res.F = s.F * L * vd.out_scale;
-    pose_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
+    if (MODE == kGeoGrad) {
+      geometry_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
+      res.J[3] = res.J[4] = res.J[5] = 0.f;
+    } else {
+      pose_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
+    }
   } else if (MODE == kBackproject) {
     walk_backproject(vd, r, gscale * L, gvol);
   }
 }
 
+// Persistent walk kernel: each warp claims 8x4-pixel tiles (pose-major order)
+// from a per-launch counter until the batch runs out, so no warp slot idles
+// while a slower warp of its block finishes, and the grid is exactly what the
+// GPU holds at once.  A warp copies its pose's geometry to its own shared slot
+// when the pose changes.  Pose-gradient mode writes one partial sum of g . J
+// per tile, so the result does not depend on which warp took which tile.
 template <int MODE, int DT>
-__global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGrad) ? DRR_JAC_MINB : DRR_FWD_MINB)
-    siddon_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs,
-                                                          float* __restrict__ out, float* __restrict__ jac,
-                                                          const float* __restrict__ gin,
-                                                          float* __restrict__ partials, float* __restrict__ gvol) {
-  __shared__ PoseGeom spg;
-  __shared__ float red[kThreads / 32][6];
+__global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGrad || MODE == kGeoGrad) ? DRR_JAC_MINB
+                                                                                                : DRR_FWD_MINB)
+    siddon_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs, int B, unsigned int* __restrict__ counter,
+                  float* __restrict__ out, float* __restrict__ jac, const float* __restrict__ gin,
+                  float* __restrict__ partials, float* __restrict__ gvol) {
+  __shared__ PoseGeom spg[kThreads / 32];
   __shared__ typename ScratchFor<MODE>::type ws;
-  const int b = blockIdx.z;
-  {
-    const unsigned int* src = reinterpret_cast<const unsigned int*>(pgs + b);
-    unsigned int* dst = reinterpret_cast<unsigned int*>(&spg);
-    for (int i = threadIdx.x; i < static_cast<int>(sizeof(PoseGeom) / 4); i += kThreads) dst[i] = src[i];
-  }
-  __syncthreads();
-  int h, w;
-  tile_pixel(blockIdx.x, blockIdx.y, threadIdx.x, &h, &w);
-  const bool valid = (w < det.W) && (h < det.H);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int twx = (det.W + kWarpTileW - 1) / kWarpTileW;
+  const int per_pose = twx * ((det.H + kWarpTileH - 1) / kWarpTileH);
+  const unsigned int total = static_cast<unsigned int>(per_pose) * static_cast<unsigned int>(B);
   const size_t npix = static_cast<size_t>(det.H) * det.W;
-  const size_t pix = static_cast<size_t>(h) * det.W + w;
-
-  RayResult r;
-  r.nseg = 0;
-  float gsc = 0.f;
-  if (valid && (MODE == kPoseGrad || MODE == kBackproject)) gsc = gin[b * npix + pix];
-  if (valid && !(MODE == kBackproject && gsc == 0.f)) {
-    trace_ray<MODE, DT>(vd, spg, h, w, gsc, gvol, &ws, r);
-  } else {
-    r.F = 0.f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) r.J[k] = 0.f;
-  }
-  if (MODE == kCount) {
-    if (valid) reinterpret_cast<int*>(out)[b * npix + pix] = r.nseg;
-  } else if (MODE == kFwd || MODE == kFwdJac) {
-    if (valid) {
-      out[b * npix + pix] = r.F;
-      if (MODE == kFwdJac) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) jac[(static_cast<size_t>(b) * 6 + k) * npix + pix] = r.J[k];
-      }
+  PoseGeom& pg = spg[warp];
+  int cur = -1;
+  for (;;) {
+    unsigned int tile = 0u;
+    if (lane == 0) tile = atomicAdd(counter, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);  // also: every lane is done with the previous tile
+    if (tile >= total) break;
+    const int b = static_cast<int>(tile / static_cast<unsigned int>(per_pose));
+    const int tin = static_cast<int>(tile) - b * per_pose;
+    if (b != cur) {
+      const unsigned int* src = reinterpret_cast<const unsigned int*>(pgs + b);
+      unsigned int* dst = reinterpret_cast<unsigned int*>(&pg);
+      for (int i = lane; i < static_cast<int>(sizeof(PoseGeom) / 4); i += 32) dst[i] = src[i];
+      __syncwarp();
+      cur = b;
     }
-  } else if (MODE == kPoseGrad) {
-    float c[6];
+    const int ty = tin / twx, tx = tin - ty * twx;
+    const int h = ty * kWarpTileH + lane / kWarpTileW, w = tx * kWarpTileW + lane % kWarpTileW;
+    const bool valid = (w < det.W) && (h < det.H);
+    const size_t pix = static_cast<size_t>(h) * det.W + w;
+    RayResult r;
+    r.nseg = 0;
+    float gsc = 0.f;
+    if (valid && (MODE == kPoseGrad || MODE == kGeoGrad || MODE == kBackproject)) gsc = gin[b * npix + pix];
+    if (valid && !(MODE == kBackproject && gsc == 0.f)) {
+      trace_ray<MODE, DT>(vd, pg, h, w, gsc, gvol, &ws, r);
+    } else {
+      r.F = 0.f;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) c[k] = gsc * r.J[k];
-    block_sum6(c, red);
-    if (threadIdx.x == 0) {
-      const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-      const int nblk = gridDim.x * gridDim.y;
+      for (int k = 0; k < 6; ++k) r.J[k] = 0.f;
+    }
+    if (MODE == kCount) {
+      if (valid) reinterpret_cast<int*>(out)[b * npix + pix] = r.nseg;
+    } else if (MODE == kFwd || MODE == kFwdJac) {
+      if (valid) {
+        out[b * npix + pix] = r.F;
+        if (MODE == kFwdJac) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) partials[(static_cast<size_t>(b) * nblk + blk) * 6 + k] = c[k];
+          for (int k = 0; k < 6; ++k) jac[(static_cast<size_t>(b) * 6 + k) * npix + pix] = r.J[k];
+        }
+      }
+    } else if (MODE == kPoseGrad || MODE == kGeoGrad) {
+      constexpr int nc = MODE == kPoseGrad ? 6 : 3;  // pose or detector parameters
+      float c[nc];
+#pragma unroll
+      for (int k = 0; k < nc; ++k) {
+        c[k] = gsc * r.J[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < nc; ++k) partials[(static_cast<size_t>(b) * per_pose + tin) * nc + k] = c[k];
+      }
     }
   }
 }
@@ -906,14 +976,16 @@ __global__ void __launch_bounds__(kThreads) jac_reduce_kernel(const float* __res
 }
 
 // Fixed-order FP64 sum of the per-block partials: one warp per pose.
-__global__ void pose_grad_finalize_kernel(const float* __restrict__ partials, int nblk, float* __restrict__ grad) {
+__global__ void pose_grad_finalize_kernel(const float* __restrict__ partials, int nblk, int ncol,
+                                          float* __restrict__ grad) {
   const int b = blockIdx.x, lane = threadIdx.x;
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < ncol; ++k) {
     double s = 0.0;
-    for (int c = lane; c < nblk; c += 32) s += static_cast<double>(partials[(static_cast<size_t>(b) * nblk + c) * 6 + k]);
+    for (int c = lane; c < nblk; c += 32)
+      s += static_cast<double>(partials[(static_cast<size_t>(b) * nblk + c) * ncol + k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) grad[6 * b + k] = static_cast<float>(s);
+    if (lane == 0) grad[ncol * b + k] = static_cast<float>(s);
   }
 }
 
@@ -999,13 +1071,12 @@ __device__ __forceinline__ void serve_trace(const VolumeDev& vd, const PoseGeom&
 
 // Persistent walk: blocks claim 32x8-pixel tiles of any request until the
 // tick's tiles run out; render-only tiles run the forward walk, gradient
-// tiles the Jacobian walk with the block's sum of g . J written per tile.
+// tiles the Jacobian walk with each warp's sum of g . J written per 8x4 tile.
 __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHeader* __restrict__ hdr,
                                                                  const ServeRequest* __restrict__ reqs,
                                                                  int* __restrict__ counter) {
   __shared__ PoseGeom spg;
   __shared__ ServeRequest sr;
-  __shared__ float red[kThreads / 32][6];
   __shared__ JacScratch ws;
   __shared__ int s_tile;
   const int nreq = hdr->nreq, total = hdr->total_tiles;
@@ -1026,7 +1097,8 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
     const int b = local / per_pose;
     const int tin = local - b * per_pose;
     const int ty = tin / sr.tiles_x, tx = tin - ty * sr.tiles_x;
-    {
+    const bool in_range = b >= 0 && b < sr.B;  // the tick table's tile ranges, checked
+    if (in_range) {
       const unsigned int* src = reinterpret_cast<const unsigned int*>(sr.geom + b);
       unsigned int* dst = reinterpret_cast<unsigned int*>(&spg);
       for (int i = threadIdx.x; i < static_cast<int>(sizeof(PoseGeom) / 4); i += kThreads) dst[i] = src[i];
@@ -1034,7 +1106,7 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
     __syncthreads();
     int h, w;
     tile_pixel(tx, ty, threadIdx.x, &h, &w);
-    const bool valid = (w < sr.det.W) && (h < sr.det.H);
+    const bool valid = in_range && (w < sr.det.W) && (h < sr.det.H);
     const size_t npix = static_cast<size_t>(sr.det.H) * sr.det.W;
     const size_t pix = static_cast<size_t>(h) * sr.det.W + w;
     const bool want_grad = sr.grad != nullptr;
@@ -1052,14 +1124,23 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
       }
       sr.out[b * npix + pix] = res.F;
     }
-    if (want_grad) {  // uniform across the block
+    if (want_grad && in_range) {  // uniform across the block
+      // one partial per 8x4 warp tile, numbered as in siddon_kernel, so that the
+      // fixed-order finalize gives the same bits as a direct render_backward
       float c[6];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) c[k] = gsc * res.J[k];
-      block_sum6(c, red);
-      if (threadIdx.x == 0) {
+      for (int k = 0; k < 6; ++k) {
+        c[k] = gsc * res.J[k];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) sr.partials[(static_cast<size_t>(b) * per_pose + tin) * 6 + k] = c[k];
+        for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+      }
+      const int warp = threadIdx.x >> 5;
+      const int wtx = tx * kWarpsX + warp % kWarpsX, wty = ty * (kTileH / kWarpTileH) + warp / kWarpsX;
+      const int twx = (sr.det.W + kWarpTileW - 1) / kWarpTileW;
+      if ((threadIdx.x & 31) == 0 && wtx * kWarpTileW < sr.det.W && wty * kWarpTileH < sr.det.H) {
+        const size_t slot = static_cast<size_t>(b) * pose_tiles(sr.det) + static_cast<size_t>(wty) * twx + wtx;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sr.partials[slot * 6 + k] = c[k];
       }
     }
     __syncthreads();  // shared request / pose data is rewritten for the next tile
@@ -1075,7 +1156,7 @@ __global__ void serve_finalize_kernel(const ServeHeader* __restrict__ hdr, const
     const ServeRequest& q = reqs[r];
     if (q.grad == nullptr) continue;
     const int b = i - q.pose_start;
-    const int nt = q.tiles_x * q.tiles_y;
+    const int nt = pose_tiles(q.det);
     for (int k = 0; k < 6; ++k) {
       double s = 0.0;
       for (int c = lane; c < nt; c += 32) s += static_cast<double>(q.partials[(static_cast<size_t>(b) * nt + c) * 6 + k]);
@@ -1092,22 +1173,44 @@ int grid_for(int64_t n, int threads) {
   return static_cast<int>(g < 1 ? 1 : g);
 }
 
+// Blocks of one walk-kernel instance that fit on the device at once (cached per device).
+template <int MODE, int DT>
+int resident_blocks() {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = 0;
+  if (cache[dev] == 0) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, siddon_kernel<MODE, DT>, kThreads, 0);
+    cache[dev] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  }
+  return cache[dev];
+}
+
+template <int MODE, int DT>
+cudaError_t launch_siddon_dt(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, unsigned int* counter,
+                             float* out, float* jac, const float* gin, float* partials, float* gvol,
+                             cudaStream_t stream) {
+  const int64_t tiles = static_cast<int64_t>(pose_tiles(det)) * B;
+  const int64_t want = (tiles + kThreads / 32 - 1) / (kThreads / 32);
+  const int grid = static_cast<int>(std::min<int64_t>(want, resident_blocks<MODE, DT>()));
+  siddon_kernel<MODE, DT><<<grid, kThreads, 0, stream>>>(vd, det, pg, B, counter, out, jac, gin, partials, gvol);
+  return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_siddon(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
                           const float* gin, float* partials, float* gvol, cudaStream_t stream) {
-  dim3 grid((det.W + kTileW - 1) / kTileW, (det.H + kTileH - 1) / kTileH, B);
+  // one counter per walk kind, so a geometry can serve one launch of each
+  const int slot = MODE == kPoseGrad ? 1 : (MODE == kBackproject ? 2 : (MODE == kGeoGrad ? 3 : 0));
+  unsigned int* counter = reinterpret_cast<unsigned int*>(const_cast<PoseGeom*>(pg) + B) + slot;
   switch (vd.dtype) {
-    case kF32:
-      siddon_kernel<MODE, kF32><<<grid, kThreads, 0, stream>>>(vd, det, pg, out, jac, gin, partials, gvol);
-      break;
-    case kBF16:
-      siddon_kernel<MODE, kBF16><<<grid, kThreads, 0, stream>>>(vd, det, pg, out, jac, gin, partials, gvol);
-      break;
-    default:
-      siddon_kernel<MODE, kF16><<<grid, kThreads, 0, stream>>>(vd, det, pg, out, jac, gin, partials, gvol);
-      break;
+    case kF32: return launch_siddon_dt<MODE, kF32>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream);
+    case kBF16: return launch_siddon_dt<MODE, kBF16>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream);
+    default: return launch_siddon_dt<MODE, kF16>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -1135,7 +1238,7 @@ int pose_grad_blocks(const DetDev& det, bool from_jacobian) {
     const int npix = det.H * det.W;
     return (npix + kThreads * kJacPixPerThread - 1) / (kThreads * kJacPixPerThread);
   }
-  return ((det.W + kTileW - 1) / kTileW) * ((det.H + kTileH - 1) / kTileH);
+  return pose_tiles(det);
 }
 
 cudaError_t launch_pose_grad_partials(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
@@ -1162,7 +1265,15 @@ cudaError_t launch_jac_reduce(const DetDev& det, int B, const float* grad_drr, c
 }
 
 cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream) {
-  pose_grad_finalize_kernel<<<B, 32, 0, stream>>>(partials, nblk, grad_pose);
+  pose_grad_finalize_kernel<<<B, 32, 0, stream>>>(partials, nblk, 6, grad_pose);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geometry_grad(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
+                                 const float* grad_drr, float* partials, float* grad_geometry, cudaStream_t stream) {
+  cudaError_t e = launch_siddon<kGeoGrad>(vd, det, pg, B, nullptr, nullptr, grad_drr, partials, nullptr, stream);
+  if (e != cudaSuccess) return e;
+  pose_grad_finalize_kernel<<<B, 32, 0, stream>>>(partials, pose_tiles(det), 3, grad_geometry);
   return cudaGetLastError();
 }
 

@@ -41,13 +41,15 @@ __device__ __forceinline__ void block_sums(double (&v)[N], double (*sm)[N]) {
 // s = sqrt(mean(c^2)), I^ = c / (s + eps) (same for the fixed image F):
 //   zncc = mean(I^ F^),  loss = -zncc,
 //   d zncc / dI_j = (F^_j - zncc c_j / s) / (N (s + eps)).
+// fixed_stride: elements between consecutive fixed images (0: one fixed image for all).
 __global__ void __launch_bounds__(kZThreads) zncc_kernel(const float* __restrict__ moving,
-                                                         const float* __restrict__ fixed, int npix, float eps,
-                                                         float* __restrict__ loss, float* __restrict__ grad) {
+                                                         const float* __restrict__ fixed, size_t fixed_stride,
+                                                         int npix, float eps, float* __restrict__ loss,
+                                                         float* __restrict__ grad) {
   __shared__ double sm[kZThreads / 32][5];
   const size_t base = static_cast<size_t>(blockIdx.x) * npix;
   const float* I = moving + base;
-  const float* F = fixed + base;
+  const float* F = fixed + static_cast<size_t>(blockIdx.x) * fixed_stride;
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // sum I, sum I^2, sum F, sum F^2, sum I F
   for (int i = threadIdx.x; i < npix; i += kZThreads) {
     const double a = I[i], b = F[i];
@@ -95,14 +97,19 @@ __global__ void adam_kernel(float* __restrict__ params, const float* __restrict_
 
 }  // namespace
 
+cudaError_t drr::launch_zncc(const float* moving, const float* fixed, size_t fixed_stride, int B, int npix, float eps,
+                             float* loss, float* grad, cudaStream_t stream) {
+  zncc_kernel<<<B, kZThreads, 0, stream>>>(moving, fixed, fixed_stride, npix, eps, loss, grad);
+  return cudaGetLastError();
+}
+
 extern "C" drr_status drr_zncc(const float* moving_dev, const float* fixed_dev, int32_t B, int32_t npix,
                                float eps, float* loss_dev, float* grad_dev, void* cuda_stream) {
   if (B <= 0 || npix <= 0) return drr::set_error(DRR_ERR_INVALID, "B and npix must be positive");
   if (!moving_dev || !fixed_dev || (!loss_dev && !grad_dev)) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   if (!(eps >= 0.f)) return drr::set_error(DRR_ERR_INVALID, "eps must be >= 0");
-  zncc_kernel<<<B, kZThreads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(moving_dev, fixed_dev, npix, eps, loss_dev,
-                                                                           grad_dev);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = drr::launch_zncc(moving_dev, fixed_dev, static_cast<size_t>(npix), B, npix, eps, loss_dev, grad_dev,
+                                   static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return drr::cuda_error(e, "zncc launch");
   drr::count_launches(1);
   return DRR_OK;

@@ -77,7 +77,7 @@ struct Tick {
 // Sizes of a request's device and staging buffers (each piece 256-B aligned).
 void size_request(Req& q) {
   const size_t B = static_cast<size_t>(q.r.B);
-  const size_t nt = static_cast<size_t>(q.tiles_x) * q.tiles_y;
+  const size_t nt = static_cast<size_t>(drr::pose_tiles(q.det));  // gradient partials per pose
   q.dev_bytes = up(B * 6 * 4) + up(B * q.npix * 4) + up(B * sizeof(drr::PoseGeom));
   q.host_bytes = up(B * 6 * 4) + up(B * q.npix * 4);
   if (q.grad) {
@@ -190,7 +190,9 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   for (size_t i = 0; i < batch.size(); ++i) {
     Req* q = batch[i];
     q->tick = t->id;
-    const size_t B = static_cast<size_t>(q->r.B), nt = static_cast<size_t>(q->tiles_x) * q->tiles_y;
+    const size_t B = static_cast<size_t>(q->r.B);
+    const size_t nt = static_cast<size_t>(drr::pose_tiles(q->det));        // gradient partials per pose
+    const size_t nblk = static_cast<size_t>(q->tiles_x) * q->tiles_y;      // walk work tiles per pose
     char* d = dev_base + q->dev_off;
     char* h = host_base + q->host_off;
     q->d_poses = reinterpret_cast<float*>(d); d += up(B * 6 * 4);
@@ -222,7 +224,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     sr.tiles_y = q->tiles_y;
     sr.tile_start = tile_start;
     sr.pose_start = pose_start;
-    tile_start += static_cast<int>(B * nt);
+    tile_start += static_cast<int>(B * nblk);
     pose_start += static_cast<int>(B);
   }
   hdr->nreq = static_cast<int>(batch.size());

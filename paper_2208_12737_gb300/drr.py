@@ -29,6 +29,7 @@ EXPORTS = (
     "drr_server_create", "drr_server_submit", "drr_server_wait", "drr_server_cancel", "drr_server_get_stats",
     "drr_server_pause", "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
     "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc", "drr_zncc", "drr_adam_step",
+    "drr_loss_landscape", "drr_geometry_grad",
 )
 
 
@@ -124,6 +125,9 @@ def load(path: str = LIB_PATH):
         lib.drr_arena_destroy.argtypes = [_vp]
         lib.drr_pose_grad_noalloc.argtypes = [ctypes.POINTER(drr_detector), _i32, _vp, _vp, _vp, _vp]
         lib.drr_zncc.argtypes = [_vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _vp]
+        lib.drr_geometry_grad.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp, _vp]
+        lib.drr_loss_landscape.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _vp, _i32, ctypes.c_float, _vp,
+                                           _i32, _vp]
         lib.drr_adam_step.argtypes = [_vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]
         for name in EXPORTS:
@@ -331,6 +335,38 @@ def zncc(moving, fixed, eps: float = 1e-8, grad: bool = True, stream=None):
     check(lib.drr_zncc(mp, fp, B, npix, float(eps), ctypes.c_void_p(loss.data_ptr()),
                        ctypes.c_void_p(g.data_ptr()) if grad else None, _stream_ptr(stream)))
     return (loss, g) if grad else loss
+
+
+def geometry_grad(volume: Volume, det, poses, grad_drr, stream=None):
+    """dL/d(sdr, delta_h, delta_w) per pose (B, 3): the gradient with respect to the detector
+    parameters for an upstream gradient grad_drr (B, H, W)."""
+    import torch
+    lib = load()
+    d = detector(det)
+    B = poses.shape[0]
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
+    gp = _dev_ptr(grad_drr, torch.float32, (B, d.height, d.width), "grad_drr")
+    out = torch.empty((B, 3), device=poses.device, dtype=torch.float32)
+    check(lib.drr_geometry_grad(volume.handle, ctypes.byref(d), pp, B, gp, ctypes.c_void_p(out.data_ptr()),
+                                _stream_ptr(stream)))
+    return out
+
+
+def loss_landscape(volume: Volume, det, fixed, poses, eps: float = 1e-8, chunk: int = 0, out=None, stream=None):
+    """-ZNCC(DRR(pose_i), fixed) for each of N poses (N,), the landscape study of Sec. 3.2.
+    fixed: (H, W) float32 on the device; poses: (N, 6) float32 on the device."""
+    import torch
+    lib = load()
+    d = detector(det)
+    N = poses.shape[0]
+    pp = _dev_ptr(poses, torch.float32, (N, 6), "poses")
+    fp = _dev_ptr(fixed, torch.float32, (d.height, d.width), "fixed")
+    if out is None:
+        out = torch.empty((N,), device=poses.device, dtype=torch.float32)
+    op = _dev_ptr(out, torch.float32, (N,), "out")
+    check(lib.drr_loss_landscape(volume.handle, ctypes.byref(d), fp, pp, N, float(eps), op, int(chunk),
+                                 _stream_ptr(stream)))
+    return out
 
 
 def adam_step(params, grads, m, v, step: int, lr_rot: float, lr_trans: float, beta1: float = 0.9,
