@@ -219,6 +219,14 @@ drr_status drr_geometry_grad(drr_volume v, const drr_detector* det, const float*
 drr_status drr_loss_landscape(drr_volume v, const drr_detector* det, const float* fixed_dev, const float* poses_dev,
                               int32_t N, float eps, float* loss_out_dev, int32_t chunk, void* cuda_stream);
 
+/* Read-bandwidth probe (no counterpart in the paper; it measures the ceiling
+ * of the walk's voxel gathers, which are served from L2): streams `bytes` of
+ * buf_dev (16-byte aligned, caller-owned device memory; use a buffer smaller
+ * than L2) `reps` times with 16-byte loads cached in L2 only, on cuda_stream.
+ * Time it with events: achieved L2 read bandwidth = reps * bytes / time.
+ * sink_dev: one float the kernel may write.  Errors: DRR_ERR_INVALID, DRR_ERR_CUDA. */
+drr_status drr_probe_l2_read(const void* buf_dev, size_t bytes, int32_t reps, float* sink_dev, void* cuda_stream);
+
 /* ---- serving: continuous batching of render / render+gradient requests ---- */
 /* No counterpart in the paper (whose method is a library call); this is the
  * request loop of the serving workload.  A host thread forms "ticks": it admits

@@ -44,68 +44,73 @@ struct Voxel<kF16> {
 };
 
 // ---------------------------------------------------------------------------
-// Pose -> frame (Sec. 2.4), FP64.  R = Rz(eta0) Ry(eta1) Rx(eta2).
+// Pose -> frame (Sec. 2.4).  R = Rz(eta0) Ry(eta1) Rx(eta2).
 // ---------------------------------------------------------------------------
-__device__ void mul3(const double* A, const double* B, double* C) {
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
-}
-
-__device__ void apply3(const double* A, const double* x, double* y) {
-#pragma unroll
-  for (int r = 0; r < 3; ++r) y[r] = A[3 * r] * x[0] + A[3 * r + 1] * x[1] + A[3 * r + 2] * x[2];
-}
-
 // World-space frame of one pose: source s, pixel (0,0) centre p00, the
 // per-column and per-row pixel steps ew, eh, and optionally dR/d eta_j.
+// World-space frame of one pose: source s, pixel (0,0) centre p00, the
+// per-column and per-row pixel steps ew, eh (all FP64), and optionally R and
+// the sines / cosines of the three angles.  R = Rz Ry Rx written out.
 __device__ void pose_frame(const float* pose, const DetDev& det, double s[3], double p00[3], double ew[3],
-                           double eh[3], double sc_out[3], double pc00_out[3], double* dR /*27 or null*/) {
+                           double eh[3], double sc_out[3], double pc00_out[3], double* R_out /*9 or null*/,
+                           float* sincos_out /*6 or null: sz, cz, sy, cy, sx, cx*/) {
   double sz, cz, sy, cy, sx, cx;
   sincos(static_cast<double>(pose[0]), &sz, &cz);
   sincos(static_cast<double>(pose[1]), &sy, &cy);
   sincos(static_cast<double>(pose[2]), &sx, &cx);
-  const double Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
-  const double Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
-  const double Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
-  double T[9], R[9];
-  mul3(Rz, Ry, T);
-  mul3(T, Rx, R);
-  if (dR) {
-    const double dRz[9] = {-sz, -cz, 0, cz, -sz, 0, 0, 0, 0};
-    const double dRy[9] = {-sy, 0, cy, 0, 0, 0, -cy, 0, -sy};
-    const double dRx[9] = {0, 0, 0, 0, -sx, -cx, 0, cx, -sx};
-    double U[9];
-    mul3(dRz, Ry, U);
-    mul3(U, Rx, dR);
-    mul3(Rz, dRy, U);
-    mul3(U, Rx, dR + 9);
-    mul3(T, dRx, dR + 18);
-  }
+  const double szsy = sz * sy, czsy = cz * sy;
+  const double R[9] = {cz * cy, fma(czsy, sx, -sz * cx), fma(czsy, cx, sz * sx),
+                       sz * cy, fma(szsy, sx, cz * cx),  fma(szsy, cx, -cz * sx),
+                       -sy,     cy * sx,                 cy * cx};
   const double rho = 0.5 * static_cast<double>(det.sdr);
-  const double sc[3] = {rho, 0.0, 0.0};
-  const double pc00[3] = {-rho, -0.5 * static_cast<double>(det.W - 1) * static_cast<double>(det.dw),
-                          -0.5 * static_cast<double>(det.H - 1) * static_cast<double>(det.dh)};
-  const double vw[3] = {0.0, static_cast<double>(det.dw), 0.0};
-  const double vh[3] = {0.0, 0.0, static_cast<double>(det.dh)};
-  apply3(R, sc, s);
-  apply3(R, pc00, p00);
-  apply3(R, vw, ew);
-  apply3(R, vh, eh);
+  const double pw = -0.5 * static_cast<double>(det.W - 1) * static_cast<double>(det.dw);
+  const double ph = -0.5 * static_cast<double>(det.H - 1) * static_cast<double>(det.dh);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    s[a] += static_cast<double>(pose[3 + a]);
-    p00[a] += static_cast<double>(pose[3 + a]);
-    sc_out[a] = sc[a];
-    pc00_out[a] = pc00[a];
+    const double t = static_cast<double>(pose[3 + a]);
+    s[a] = fma(rho, R[3 * a], t);                                              // R (rho, 0, 0) + t
+    p00[a] = fma(ph, R[3 * a + 2], fma(pw, R[3 * a + 1], fma(-rho, R[3 * a], t)));  // R pc00 + t
+    ew[a] = static_cast<double>(det.dw) * R[3 * a + 1];                         // R (0, dw, 0)
+    eh[a] = static_cast<double>(det.dh) * R[3 * a + 2];                         // R (0, 0, dh)
+  }
+  sc_out[0] = rho;
+  sc_out[1] = sc_out[2] = 0.0;
+  pc00_out[0] = -rho;
+  pc00_out[1] = pw;
+  pc00_out[2] = ph;
+  if (R_out) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) R_out[i] = R[i];
+  }
+  if (sincos_out) {
+    sincos_out[0] = static_cast<float>(sz);
+    sincos_out[1] = static_cast<float>(cz);
+    sincos_out[2] = static_cast<float>(sy);
+    sincos_out[3] = static_cast<float>(cy);
+    sincos_out[4] = static_cast<float>(sx);
+    sincos_out[5] = static_cast<float>(cx);
   }
 }
 
-// Per-pose geometry in the volume's voxel units plus the chain-rule terms.
+__device__ void mul3f(const float* A, const float* B, float* C) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) C[3 * r + c] = fmaf(A[3 * r], B[c], fmaf(A[3 * r + 1], B[3 + c], A[3 * r + 2] * B[6 + c]));
+}
+
+__device__ void apply3f(const float* A, const float* x, float* y) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) y[r] = fmaf(A[3 * r], x[0], fmaf(A[3 * r + 1], x[1], A[3 * r + 2] * x[2]));
+}
+
+// Per-pose geometry in the volume's voxel units plus the chain-rule terms.  The
+// ray geometry is FP64; the chain-rule terms are stored as FP32 and computed in
+// FP32 (dR/d eta_j from the FP32-rounded sines and cosines).
 __device__ void compute_pose_geom(const float* pose, const DetDev& det, const VolumeDev& vd, PoseGeom& g) {
-  double s[3], p00[3], ew[3], eh[3], sc[3], pc00[3], dR[27];
-  pose_frame(pose, det, s, p00, ew, eh, sc, pc00, dR);
+  double s[3], p00[3], ew[3], eh[3], sc[3], pc00[3], R[9];
+  float cs[6];
+  pose_frame(pose, det, s, p00, ew, eh, sc, pc00, R, cs);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double dl = static_cast<double>(vd.delta[a]);
@@ -118,30 +123,37 @@ __device__ void compute_pose_geom(const float* pose, const DetDev& det, const Vo
     g.gw[a] = ew[a] / dl;
     g.gh[a] = eh[a] / dl;
   }
-  // R e_x = (s - t) / rho, R e_y = ew / dw, R e_z = eh / dh
-  const double rho = sc[0];
+  // columns of R (R e_x, R e_y, R e_z) for the detector-parameter chain
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    g.Rc[0][a] = static_cast<float>((s[a] - static_cast<double>(pose[3 + a])) / rho);
-    g.Rc[1][a] = static_cast<float>(ew[a] / static_cast<double>(det.dw));
-    g.Rc[2][a] = static_cast<float>(eh[a] / static_cast<double>(det.dh));
-  }
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g.Rc[c][a] = static_cast<float>(R[3 * a + c]);
   g.hc = 0.5f * static_cast<float>(det.H - 1);
   g.wc = 0.5f * static_cast<float>(det.W - 1);
-  const double q[3] = {pc00[0] - sc[0], pc00[1] - sc[1], pc00[2] - sc[2]};
-  const double vw[3] = {0.0, static_cast<double>(det.dw), 0.0};
-  const double vh[3] = {0.0, 0.0, static_cast<double>(det.dh)};
+  const float sz = cs[0], cz = cs[1], sy = cs[2], cy = cs[3], sx = cs[4], cx = cs[5];
+  const float Rz[9] = {cz, -sz, 0.f, sz, cz, 0.f, 0.f, 0.f, 1.f};
+  const float Ry[9] = {cy, 0.f, sy, 0.f, 1.f, 0.f, -sy, 0.f, cy};
+  const float Rx[9] = {1.f, 0.f, 0.f, 0.f, cx, -sx, 0.f, sx, cx};
+  const float dRz[9] = {-sz, -cz, 0.f, cz, -sz, 0.f, 0.f, 0.f, 0.f};
+  const float dRy[9] = {-sy, 0.f, cy, 0.f, 0.f, 0.f, -cy, 0.f, -sy};
+  const float dRx[9] = {0.f, 0.f, 0.f, 0.f, -sx, -cx, 0.f, cx, -sx};
+  float T[9], U[9], dR[27];
+  mul3f(Rz, Ry, T);
+  mul3f(dRz, Ry, U);
+  mul3f(U, Rx, dR);
+  mul3f(Rz, dRy, U);
+  mul3f(U, Rx, dR + 9);
+  mul3f(T, dRx, dR + 18);
+  const float scf[3] = {static_cast<float>(sc[0]), 0.f, 0.f};
+  const float q[3] = {static_cast<float>(pc00[0] - sc[0]), static_cast<float>(pc00[1]), static_cast<float>(pc00[2])};
+  const float vw[3] = {0.f, det.dw, 0.f};
+  const float vh[3] = {0.f, 0.f, det.dh};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    double t[3];
-    apply3(dR + 9 * j, sc, t);
-    for (int a = 0; a < 3; ++a) g.S[j][a] = static_cast<float>(t[a]);
-    apply3(dR + 9 * j, q, t);
-    for (int a = 0; a < 3; ++a) g.Q[j][a] = static_cast<float>(t[a]);
-    apply3(dR + 9 * j, vw, t);
-    for (int a = 0; a < 3; ++a) g.Wv[j][a] = static_cast<float>(t[a]);
-    apply3(dR + 9 * j, vh, t);
-    for (int a = 0; a < 3; ++a) g.Hv[j][a] = static_cast<float>(t[a]);
+    apply3f(dR + 9 * j, scf, g.S[j]);
+    apply3f(dR + 9 * j, q, g.Q[j]);
+    apply3f(dR + 9 * j, vw, g.Wv[j]);
+    apply3f(dR + 9 * j, vh, g.Hv[j]);
   }
 }
 
@@ -164,7 +176,7 @@ __global__ void ray_setup_kernel(const float* __restrict__ poses, int B, DetDev 
   const int q = static_cast<int>(i % npix);
   const int h = q / det.W, w = q % det.W;
   double s[3], p00[3], ew[3], eh[3], sc[3], pc00[3];
-  pose_frame(poses + 6 * b, det, s, p00, ew, eh, sc, pc00, nullptr);
+  pose_frame(poses + 6 * b, det, s, p00, ew, eh, sc, pc00, nullptr, nullptr);
   float* r = rays + 6 * i;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -354,7 +366,7 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 // position of the current point, so local positions stay below ~kChunk plane
 // gaps and carry ~2^-29 of the span in absolute precision instead of the
 // 2^-24 * alpha of a whole-ray FP32 walk.  Positions are in fixed-point high-word
-// units (span / 2^30).
+// units (span / 2^29).
 // ---------------------------------------------------------------------------
 #ifndef DRR_CHUNK
 #define DRR_CHUNK 32
@@ -368,7 +380,18 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 #ifndef DRR_JAC_MINB
 #define DRR_JAC_MINB 4
 #endif
-constexpr int kChunk = DRR_CHUNK;  // 32: local positions stay below ~32 plane gaps
+// Forward walk chunk, per ray: the FP32 error of a local position grows with
+// the chunk's share of the ray (chunk / segments), so long rays take longer
+// chunks (fewer exact re-anchorings) and short rays shorter ones.  DRR_CHUNK is
+// the chunk of a ray with 256 to 512 segments; all four are multiples of the unroll.
+constexpr int kChunk = DRR_CHUNK;
+#ifndef DRR_FWD_ADAPTIVE
+#define DRR_FWD_ADAPTIVE 1
+#endif
+__device__ __forceinline__ int fwd_chunk(int nseg) {
+  return DRR_FWD_ADAPTIVE ? (nseg > 512 ? 2 * kChunk : nseg > 256 ? kChunk : nseg > 128 ? kChunk / 2 : kChunk / 4)
+                          : kChunk;
+}
 constexpr int kUnroll = DRR_UNROLL;
 constexpr float kTwoM32 = 2.3283064365386963e-10f;  // 2^-32
 
@@ -422,8 +445,20 @@ constexpr int kJacUnroll = DRR_JAC_UNROLL;
 #define DRR_JAC_CHUNK 31
 #endif
 // Jacobian chunk length: the first crossing of a chunk is peeled, so the
-// unrolled loop runs kJacChunk - 1 = 30 times, a whole number of unrolled bodies.
+// unrolled loop runs chunk - 1 times; 61, 31, 19 and 13 keep that a whole
+// number of unrolled bodies.
 constexpr int kJacChunk = DRR_JAC_CHUNK;
+#ifndef DRR_JAC_ADAPTIVE
+#define DRR_JAC_ADAPTIVE 1
+#endif
+// Jacobian chunk per ray, as for the forward walk: 6k + 1 crossings (61, 31, 19, 13).
+__device__ __forceinline__ int jac_chunk(int nseg) {
+  return DRR_JAC_ADAPTIVE ? (nseg > 512   ? 2 * kJacChunk - 1
+                             : nseg > 256 ? kJacChunk
+                             : nseg > 128 ? (kJacChunk + 7) / 2
+                                          : (kJacChunk + 7) / 2 - 6)
+                          : kJacChunk;
+}
 
 template <int DT>
 __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetup& r, WalkScratch* ws) {
@@ -441,6 +476,7 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
   float v = Voxel<DT>::load(vd.data, off);
   float acc = 0.f;
   int remaining = r.nseg - 1;
+  const int chunk = fwd_chunk(r.nseg);
   for (;;) {
     const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], kx), O);
     const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], ky), O);
@@ -448,7 +484,7 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
     float tx = x0, ty = y0, tz = z0;
     float lx = 0.f, ly = 0.f, lz = 0.f;
     float ac = 0.f;
-    const int n = min(remaining, kChunk);
+    const int n = min(remaining, chunk);
 #pragma unroll kUnroll
     for (int m = 0; m < n; ++m) {
       const float an = fminf(fminf(tx, ty), tz);
@@ -546,8 +582,9 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
   bool p0 = r.ea == a0, p1 = r.ea == a1;
   if (r.ea < 0) Gc = -v;  // entry clamped at alpha 0: weight -V_first
   int remaining = r.nseg - 1;
+  const int chunk = jac_chunk(r.nseg);
   while (remaining > 0) {
-    const int n = min(remaining, kJacChunk);
+    const int n = min(remaining, chunk);
     ws->c_off[t] = off;
     ws->c_v[t] = v;
     ws->c_vprev[t] = vprev;

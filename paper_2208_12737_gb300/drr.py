@@ -29,7 +29,7 @@ EXPORTS = (
     "drr_server_create", "drr_server_submit", "drr_server_wait", "drr_server_cancel", "drr_server_get_stats",
     "drr_server_pause", "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
     "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc", "drr_zncc", "drr_adam_step",
-    "drr_loss_landscape", "drr_geometry_grad",
+    "drr_loss_landscape", "drr_geometry_grad", "drr_probe_l2_read",
 )
 
 
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
         lib.drr_arena_destroy.argtypes = [_vp]
         lib.drr_pose_grad_noalloc.argtypes = [ctypes.POINTER(drr_detector), _i32, _vp, _vp, _vp, _vp]
         lib.drr_zncc.argtypes = [_vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _vp]
+        lib.drr_probe_l2_read.argtypes = [_vp, ctypes.c_size_t, _i32, _vp, _vp]
         lib.drr_geometry_grad.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp, _vp]
         lib.drr_loss_landscape.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _vp, _i32, ctypes.c_float, _vp,
                                            _i32, _vp]
@@ -350,6 +351,13 @@ def geometry_grad(volume: Volume, det, poses, grad_drr, stream=None):
     check(lib.drr_geometry_grad(volume.handle, ctypes.byref(d), pp, B, gp, ctypes.c_void_p(out.data_ptr()),
                                 _stream_ptr(stream)))
     return out
+
+
+def probe_l2_read(buf, reps: int, sink, stream=None):
+    """Stream a device buffer (uint8/float tensor, 16-byte aligned) reps times from L2."""
+    lib = load()
+    check(lib.drr_probe_l2_read(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(), int(reps),
+                                ctypes.c_void_p(sink.data_ptr()), _stream_ptr(stream)))
 
 
 def loss_landscape(volume: Volume, det, fixed, poses, eps: float = 1e-8, chunk: int = 0, out=None, stream=None):
