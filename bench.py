@@ -422,6 +422,65 @@ def vgs_baseline(drr, hu, cfg, poses, E_ours, rays, reps=2):
                     "clamp, sort, Eq. 2 on midpoints), 4 poses per pass"}
 
 
+def plain_fp32_baseline(drr, vol, det, poses, E_ours, rays, reps=5):
+    """The plain FP32 forward walk on the same batch (the comparison baseline), with its
+    largest relative difference from the product kernel's DRR (1e-3 * max floor)."""
+    import torch
+    out = torch.empty_like(E_ours)
+    drr.render_plain_fp32(vol, det, poses, out=out)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        drr.render_plain_fp32(vol, det, poses, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    ref = E_ours.double()
+    floor = 1e-3 * ref.abs().max()
+    diff = float(((out.double() - ref).abs() / torch.maximum(ref.abs(), floor)).max())
+    return {"ms_per_step": t, "value": rays / (t * 1e-3) / 1e9, "unit": UNIT, "max_rel_diff_vs_kernel": diff,
+            "what": "forward only: textbook incremental Siddon-Jacobs walk, all FP32, thread per ray, linear layout"}
+
+
+def precision_bench(drr, reps=3):
+    """The precision-sweep workload (512^3 at 0.5 mm, 1024x1024 at 0.4 mm, 8 poses): forward
+    throughput per storage dtype and the largest relative difference from the FP32-storage DRR
+    (the errors against the FP64 oracle are the parity tests' business)."""
+    import torch
+    from paper_2208_12737_gb300 import inputs
+    cfg = inputs.PRECISION
+    vol_np = inputs.bone_tissue_phantom(cfg["shape_zyx"], cfg["spacing"], seed=cfg["phantom_seed"])
+    det = cfg["detector"]
+    poses = torch.from_numpy(inputs.random_poses(cfg["batch"], seed=cfg["pose_seed"])).cuda()
+    rays = cfg["batch"] * det.height * det.width
+    res = {}
+    E32 = None
+    for storage in ("f32", "bf16", "f16"):
+        v = drr.Volume(vol_np, cfg["spacing"], storage=storage)
+        E = drr.render(v, det, poses)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            drr.render(v, det, poses, out=E)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.median(ms)
+        if E32 is None:
+            E32 = E.double()
+        floor = 1e-3 * E32.abs().max()
+        res[storage] = {"fwd_ms": t, "grays_per_s": rays / (t * 1e-3) / 1e9,
+                        "max_rel_diff_vs_f32": float(((E.double() - E32).abs() / torch.maximum(E32.abs(), floor)).max())}
+        v.close()
+    res["workload"] = "512^3 at 0.5 mm (air / soft tissue 0.02 / bone 0.04-0.06 per mm), 1024x1024 at 0.4 mm, 8 poses"
+    return res
+
+
 def fd_baseline(drr, vol, det, poses, rays, reps=3):
     """The finite-difference alternative to the analytic pose gradient: central differences
     need 12 extra forward renders per pose (13 with the DRR itself), timed as one batch."""
@@ -636,13 +695,18 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed": wall,
     }
-    line["fd_baseline"] = fd_baseline(drr, vol, det, poses, rays)
-    if not args.no_vgs:
+    if not args.no_baselines:
+        l2 = l2_read_gbs(drr)
+        line["roofline"]["gather"] = {"achieved_gbs": gather_gbs, "peak_gbs": l2, "frac": gather_gbs / l2,
+                                      "peak_source": "measured: 64 MB L2-resident buffer streamed with 16-byte loads"}
+        line["fd_baseline"] = fd_baseline(drr, vol, det, poses, rays)
         drr.render(vol, det, poses, out=E)
-        line["vgs_torch_baseline"] = vgs_baseline(drr, hu, cfg, poses, E, rays)
-    l2 = l2_read_gbs(drr)
-    line["roofline"]["gather"] = {"achieved_gbs": gather_gbs, "peak_gbs": l2, "frac": gather_gbs / l2,
-                                  "peak_source": "measured: 64 MB L2-resident buffer streamed with 16-byte loads"}
+        line["plain_fp32_baseline"] = plain_fp32_baseline(drr, vol, det, poses, E, rays)
+        if not args.no_vgs:
+            drr.render(vol, det, poses, out=E)
+            line["vgs_torch_baseline"] = vgs_baseline(drr, hu, cfg, poses, E, rays)
+    if not args.no_precision:
+        line["precision"] = precision_bench(drr)
     if not args.no_registration:
         line["registration"] = registration_bench(drr, hu)
     if not args.no_landscape:
@@ -674,6 +738,9 @@ def main():
     ap.add_argument("--no-registration", action="store_true")
     ap.add_argument("--no-landscape", action="store_true")
     ap.add_argument("--no-vgs", action="store_true", help="skip the vectorised-tensor Siddon context line")
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="skip the L2 probe and the FD, plain-FP32 and vectorised baselines")
+    ap.add_argument("--no-precision", action="store_true", help="skip the 512^3 precision-sweep workload")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds per served load level")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

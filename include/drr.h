@@ -219,6 +219,17 @@ drr_status drr_geometry_grad(drr_volume v, const drr_detector* det, const float*
 drr_status drr_loss_landscape(drr_volume v, const drr_detector* det, const float* fixed_dev, const float* poses_dev,
                               int32_t N, float eps, float* loss_out_dev, int32_t chunk, void* cuda_stream);
 
+/* Comparison baseline, not the product path: the plain FP32 forward walk (the
+ * textbook incremental Siddon-Jacobs traversal of Sec. 2.2 with every quantity
+ * in FP32: FP32 clip, next crossings advanced by repeated FP32 addition, one
+ * thread per ray, linear volume layout, no fusion).  Same arguments and output
+ * layout as drr_render without a Jacobian.  Its error against the FP64
+ * definition is not bounded by this library's tolerances; it exists so that the
+ * product path's speed can be reported against it on the same GPU.
+ * Errors: DRR_ERR_INVALID, DRR_ERR_CUDA. */
+drr_status drr_render_plain_fp32(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
+                                 float* drr_out_dev, void* cuda_stream);
+
 /* Read-bandwidth probe (no counterpart in the paper; it measures the ceiling
  * of the walk's voxel gathers, which are served from L2): streams `bytes` of
  * buf_dev (16-byte aligned, caller-owned device memory; use a buffer smaller

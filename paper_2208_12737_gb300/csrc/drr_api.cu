@@ -120,11 +120,12 @@ struct AsyncBuf {
 // ---- kernel timing: CUDA events around each launch while enabled ----------
 enum ProfKernel {
   kPoseSetup, kSiddonFwd, kSiddonFwdJac, kSiddonPoseGrad, kJacReduce, kFinalize, kBackproject, kCountSeg, kZncc,
-  kSiddonGeoGrad, kNumProf
+  kSiddonGeoGrad, kPlainFp32, kNumProf
 };
 const char* const kProfNames[kNumProf] = {"pose_setup",        "siddon_fwd", "siddon_fwd_jac",     "siddon_pose_grad",
                                           "jac_reduce",        "pose_grad_finalize", "siddon_backproject",
-                                          "count_segments",    "zncc",       "siddon_geometry_grad"};
+                                          "count_segments",    "zncc",       "siddon_geometry_grad",
+                                          "plain_fp32_fwd"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -460,6 +461,23 @@ drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float
   if (drr_status s = setup_geometry(v, dd, poses_dev, B, st, pg)) return s;
   LaunchScope ls(kCountSeg, st);
   DRR_CUDA(drr::launch_count_segments(v->vd, dd, pg.p, B, segments_out_dev, st), "count_segments launch");
+  return DRR_OK;
+}
+
+drr_status drr_render_plain_fp32(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
+                                 float* drr_out_dev, void* cuda_stream) {
+  if (drr_status s = check_volume(v)) return s;
+  drr::DetDev dd;
+  if (drr_status s = check_detector(det, &dd)) return s;
+  if (drr_status s = check_geometry(v->vd, dd)) return s;
+  if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
+  if (!poses_dev || !drr_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  configure_pool(v->device);
+  AsyncBuf<drr::PoseGeom> pg;
+  if (drr_status s = setup_geometry(v, dd, poses_dev, B, st, pg)) return s;
+  LaunchScope ls(kPlainFp32, st);
+  DRR_CUDA(drr::launch_render_plain_fp32(v->vd, dd, pg.p, B, drr_out_dev, st), "plain FP32 render launch");
   return DRR_OK;
 }
 

@@ -114,6 +114,9 @@ cudaError_t launch_ray_setup(const float* poses, int B, const DetDev& det, float
 cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
                           cudaStream_t stream);
 // Pose gradient by re-tracing (jac == nullptr) or from a stored Jacobian.
+// Comparison baseline: the plain FP32 forward walk (out: [B][H][W]).
+cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out,
+                                     cudaStream_t stream);
 // Negative ZNCC of B moving images against fixed images fixed_stride elements
 // apart (0: one fixed image for all), and optionally d loss / d moving.
 cudaError_t launch_zncc(const float* moving, const float* fixed, size_t fixed_stride, int B, int npix, float eps,

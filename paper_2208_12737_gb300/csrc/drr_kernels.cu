@@ -1250,7 +1250,94 @@ cudaError_t launch_siddon(const VolumeDev& vd, const DetDev& det, const PoseGeom
   }
 }
 
+// ---------------------------------------------------------------------------
+// Comparison baseline: the plain FP32 forward path.  The textbook incremental
+// Siddon-Jacobs walk (Sec. 2.2, Eq. 2-3) entirely in FP32: one thread per ray
+// in 16x16 blocks, FP32 clip (Sec. 2.3), each axis' next crossing advanced by
+// repeated FP32 addition, the voxel of the first segment from its midpoint.
+// It is what the product walk is measured against; its rounding drift is
+// why the product walk anchors its crossings in fixed point.
+// ---------------------------------------------------------------------------
+template <int DT>
+__global__ void __launch_bounds__(256) plain_fp32_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs,
+                                                         float* __restrict__ out) {
+  const int w = blockIdx.x * 16 + (threadIdx.x & 15), h = blockIdx.y * 16 + (threadIdx.x >> 4), b = blockIdx.z;
+  if (w >= det.W || h >= det.H) return;
+  const PoseGeom& pg = pgs[b];
+  float u0[3], g[3], amin = 0.f, amax = 1.f;
+  bool hit = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u0[a] = pg.u0f[a];
+    g[a] = static_cast<float>(pg.g00[a]) + static_cast<float>(w) * static_cast<float>(pg.gw[a]) +
+           static_cast<float>(h) * static_cast<float>(pg.gh[a]);
+    if (g[a] != 0.f) {
+      const float t0 = -u0[a] / g[a], t1 = (static_cast<float>(vd.n[a]) - u0[a]) / g[a];
+      amin = fmaxf(amin, fminf(t0, t1));
+      amax = fminf(amax, fmaxf(t0, t1));
+    } else if (!(u0[a] >= 0.f && u0[a] < static_cast<float>(vd.n[a]))) {
+      hit = false;
+    }
+  }
+  float acc = 0.f;
+  if (hit && amin < amax) {
+    float an[3], da[3];
+    int idx[3], st[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float ue = u0[a] + amin * g[a];
+      if (g[a] > 0.f) {
+        an[a] = (floorf(ue) + 1.f - u0[a]) / g[a];
+        da[a] = 1.f / g[a];
+        st[a] = 1;
+      } else if (g[a] < 0.f) {
+        an[a] = (ceilf(ue) - 1.f - u0[a]) / g[a];
+        da[a] = -1.f / g[a];
+        st[a] = -1;
+      } else {
+        an[a] = 2.f;
+        da[a] = 0.f;
+        st[a] = 0;
+      }
+    }
+    const float first = fminf(fminf(fminf(an[0], an[1]), an[2]), amax);
+    const float am = 0.5f * (amin + first);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) idx[a] = static_cast<int>(floorf(u0[a] + am * g[a]));
+    // scalar copies: the walk indexes no register array
+    float ax = an[0], ay = an[1], az = an[2];
+    int ix = idx[0], iy = idx[1], iz = idx[2];
+    float al = amin;
+    for (int guard = 0; guard < 4 * (vd.n[0] + vd.n[1] + vd.n[2]) + 8 && al < amax; ++guard) {
+      const float nx = fminf(fminf(fminf(ax, ay), az), amax);
+      if (ix >= 0 && ix < vd.n[0] && iy >= 0 && iy < vd.n[1] && iz >= 0 && iz < vd.n[2])
+        acc += (nx - al) * Voxel<DT>::load(vd.data, vd.origin + ix * vd.stride[0] + iy * vd.stride[1] +
+                                                         iz * vd.stride[2]);
+      al = nx;
+      const bool sx = ax == nx, sy = !sx && ay == nx, sz = !sx && !sy;
+      if (sx) { ix += st[0]; ax += da[0]; }
+      if (sy) { iy += st[1]; ay += da[1]; }
+      if (sz) { iz += st[2]; az += da[2]; }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[a] *= vd.delta[a];
+  out[(static_cast<size_t>(b) * det.H + h) * det.W + w] = acc * sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) *
+                                                          vd.out_scale;
+}
+
 }  // namespace
+
+cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out,
+                                     cudaStream_t stream) {
+  dim3 grid((det.W + 15) / 16, (det.H + 15) / 16, B);
+  switch (vd.dtype) {
+    case kF32: plain_fp32_kernel<kF32><<<grid, 256, 0, stream>>>(vd, det, pg, out); break;
+    case kBF16: plain_fp32_kernel<kBF16><<<grid, 256, 0, stream>>>(vd, det, pg, out); break;
+    default: plain_fp32_kernel<kF16><<<grid, 256, 0, stream>>>(vd, det, pg, out); break;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, const VolumeDev* vd, PoseGeom* out,
                               cudaStream_t stream) {

@@ -29,7 +29,7 @@ EXPORTS = (
     "drr_server_create", "drr_server_submit", "drr_server_wait", "drr_server_cancel", "drr_server_get_stats",
     "drr_server_pause", "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
     "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc", "drr_zncc", "drr_adam_step",
-    "drr_loss_landscape", "drr_geometry_grad", "drr_probe_l2_read",
+    "drr_loss_landscape", "drr_geometry_grad", "drr_probe_l2_read", "drr_render_plain_fp32",
 )
 
 
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
         lib.drr_arena_destroy.argtypes = [_vp]
         lib.drr_pose_grad_noalloc.argtypes = [ctypes.POINTER(drr_detector), _i32, _vp, _vp, _vp, _vp]
         lib.drr_zncc.argtypes = [_vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _vp]
+        lib.drr_render_plain_fp32.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp]
         lib.drr_probe_l2_read.argtypes = [_vp, ctypes.c_size_t, _i32, _vp, _vp]
         lib.drr_geometry_grad.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _i32, _vp, _vp, _vp]
         lib.drr_loss_landscape.argtypes = [_vp, ctypes.POINTER(drr_detector), _vp, _vp, _i32, ctypes.c_float, _vp,
@@ -350,6 +351,20 @@ def geometry_grad(volume: Volume, det, poses, grad_drr, stream=None):
     out = torch.empty((B, 3), device=poses.device, dtype=torch.float32)
     check(lib.drr_geometry_grad(volume.handle, ctypes.byref(d), pp, B, gp, ctypes.c_void_p(out.data_ptr()),
                                 _stream_ptr(stream)))
+    return out
+
+
+def render_plain_fp32(volume: Volume, det, poses, out=None, stream=None):
+    """The comparison baseline: the plain FP32 forward walk, (B, H, W)."""
+    import torch
+    lib = load()
+    d = detector(det)
+    B = poses.shape[0]
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
+    if out is None:
+        out = torch.empty((B, d.height, d.width), device=poses.device, dtype=torch.float32)
+    op = _dev_ptr(out, torch.float32, (B, d.height, d.width), "out")
+    check(lib.drr_render_plain_fp32(volume.handle, ctypes.byref(d), pp, B, op, _stream_ptr(stream)))
     return out
 
 
