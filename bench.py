@@ -481,6 +481,27 @@ def precision_bench(drr, reps=3):
     return res
 
 
+def adjoint_bench(drr, vol, det, poses, g, hu_shape, rays, reps=3):
+    """The volume adjoint (back-projection into a zeroed FP32 gradient volume, one atomic add
+    per segment) on the headline batch."""
+    import torch
+    gv = torch.zeros(hu_shape, device=poses.device, dtype=torch.float32)
+    drr.render_backward(vol, det, poses, g, pose_grad=False, grad_volume=gv)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        gv.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        drr.render_backward(vol, det, poses, g, pose_grad=False, grad_volume=gv)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    return {"ms_per_step": t, "value": rays / (t * 1e-3) / 1e9, "unit": UNIT,
+            "what": "dL/dV by back-projection (exact fixed-point re-walk, FP32 atomics) for the 16-pose batch"}
+
+
 def fd_baseline(drr, vol, det, poses, rays, reps=3):
     """The finite-difference alternative to the analytic pose gradient: central differences
     need 12 extra forward renders per pose (13 with the DRR itself), timed as one batch."""
@@ -700,6 +721,7 @@ def run_ours(args, rank, world, local_rank):
         line["roofline"]["gather"] = {"achieved_gbs": gather_gbs, "peak_gbs": l2, "frac": gather_gbs / l2,
                                       "peak_source": "measured: 64 MB L2-resident buffer streamed with 16-byte loads"}
         line["fd_baseline"] = fd_baseline(drr, vol, det, poses, rays)
+        line["volume_adjoint"] = adjoint_bench(drr, vol, det, poses, g, hu.shape, rays)
         drr.render(vol, det, poses, out=E)
         line["plain_fp32_baseline"] = plain_fp32_baseline(drr, vol, det, poses, E, rays)
         if not args.no_vgs:

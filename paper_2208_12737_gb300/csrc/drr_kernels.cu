@@ -43,6 +43,13 @@ struct Voxel<kF16> {
   }
 };
 
+// x_a for a runtime axis index without indexing a register array (which
+// would move the array to local memory).
+template <class T>
+__device__ __forceinline__ T pick3(int a, T x0, T x1, T x2) {
+  return a == 0 ? x0 : (a == 1 ? x1 : x2);
+}
+
 // ---------------------------------------------------------------------------
 // Pose -> frame (Sec. 2.4).  R = Rz(eta0) Ry(eta1) Rx(eta2).
 // ---------------------------------------------------------------------------
@@ -104,32 +111,9 @@ __device__ void apply3f(const float* A, const float* x, float* y) {
   for (int r = 0; r < 3; ++r) y[r] = fmaf(A[3 * r], x[0], fmaf(A[3 * r + 1], x[1], A[3 * r + 2] * x[2]));
 }
 
-// Per-pose geometry in the volume's voxel units plus the chain-rule terms.  The
-// ray geometry is FP64; the chain-rule terms are stored as FP32 and computed in
-// FP32 (dR/d eta_j from the FP32-rounded sines and cosines).
-__device__ void compute_pose_geom(const float* pose, const DetDev& det, const VolumeDev& vd, PoseGeom& g) {
-  double s[3], p00[3], ew[3], eh[3], sc[3], pc00[3], R[9];
-  float cs[6];
-  pose_frame(pose, det, s, p00, ew, eh, sc, pc00, R, cs);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double dl = static_cast<double>(vd.delta[a]);
-    const double lo = -0.5 * static_cast<double>(vd.n[a]) * dl;  // b_a: volume centred at the origin
-    g.u0[a] = (s[a] - lo) / dl;
-    g.un[a] = static_cast<double>(vd.n[a]) - g.u0[a];
-    g.u0f[a] = static_cast<float>(g.u0[a]);
-    g.unf[a] = static_cast<float>(g.un[a]);
-    g.g00[a] = (p00[a] - s[a]) / dl;
-    g.gw[a] = ew[a] / dl;
-    g.gh[a] = eh[a] / dl;
-  }
-  // columns of R (R e_x, R e_y, R e_z) for the detector-parameter chain
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) g.Rc[c][a] = static_cast<float>(R[3 * a + c]);
-  g.hc = 0.5f * static_cast<float>(det.H - 1);
-  g.wc = 0.5f * static_cast<float>(det.W - 1);
+// FP32 chain-rule terms of one pose (dR/d eta_j applied to s_c, p_c - s_c and the
+// pixel steps), from the FP32-rounded sines and cosines: they are stored as FP32.
+__device__ void chain_terms(const float cs[6], double rho, double pw, double ph, const DetDev& det, PoseGeom* g) {
   const float sz = cs[0], cz = cs[1], sy = cs[2], cy = cs[3], sx = cs[4], cx = cs[5];
   const float Rz[9] = {cz, -sz, 0.f, sz, cz, 0.f, 0.f, 0.f, 1.f};
   const float Ry[9] = {cy, 0.f, sy, 0.f, 1.f, 0.f, -sy, 0.f, cy};
@@ -144,28 +128,81 @@ __device__ void compute_pose_geom(const float* pose, const DetDev& det, const Vo
   mul3f(Rz, dRy, U);
   mul3f(U, Rx, dR + 9);
   mul3f(T, dRx, dR + 18);
-  const float scf[3] = {static_cast<float>(sc[0]), 0.f, 0.f};
-  const float q[3] = {static_cast<float>(pc00[0] - sc[0]), static_cast<float>(pc00[1]), static_cast<float>(pc00[2])};
+  const float scf[3] = {static_cast<float>(rho), 0.f, 0.f};
+  const float q[3] = {static_cast<float>(-2.0 * rho), static_cast<float>(pw), static_cast<float>(ph)};
   const float vw[3] = {0.f, det.dw, 0.f};
   const float vh[3] = {0.f, 0.f, det.dh};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    apply3f(dR + 9 * j, scf, g.S[j]);
-    apply3f(dR + 9 * j, q, g.Q[j]);
-    apply3f(dR + 9 * j, vw, g.Wv[j]);
-    apply3f(dR + 9 * j, vh, g.Hv[j]);
+    apply3f(dR + 9 * j, scf, g->S[j]);
+    apply3f(dR + 9 * j, q, g->Q[j]);
+    apply3f(dR + 9 * j, vw, g->Wv[j]);
+    apply3f(dR + 9 * j, vh, g->Hv[j]);
+  }
+  g->hc = 0.5f * static_cast<float>(det.H - 1);
+  g->wc = 0.5f * static_cast<float>(det.W - 1);
+}
+
+// Per-pose geometry in the volume's voxel units plus the chain-rule terms,
+// computed by a whole warp and written to *g.  The three FP64 sine/cosine pairs
+// run in lanes 0-2 and the per-axis terms in lanes 0-2: FP64 issue is narrow on
+// this GPU, and spreading the serial FP64 work over lanes shortens the kernel.
+// The arithmetic per value is that of pose_frame.
+__device__ void warp_pose_geom(const float* pose, const DetDev& det, const VolumeDev& vd, PoseGeom* g) {
+  constexpr unsigned int kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double sv = 0.0, cv = 1.0;
+  if (lane < 3) sincos(static_cast<double>(pose[lane]), &sv, &cv);
+  const double sz = __shfl_sync(kFull, sv, 0), cz = __shfl_sync(kFull, cv, 0);
+  const double sy = __shfl_sync(kFull, sv, 1), cy = __shfl_sync(kFull, cv, 1);
+  const double sx = __shfl_sync(kFull, sv, 2), cx = __shfl_sync(kFull, cv, 2);
+  const double szsy = sz * sy, czsy = cz * sy;
+  const double R[9] = {cz * cy, fma(czsy, sx, -sz * cx), fma(czsy, cx, sz * sx),
+                       sz * cy, fma(szsy, sx, cz * cx),  fma(szsy, cx, -cz * sx),
+                       -sy,     cy * sx,                 cy * cx};
+  const double rho = 0.5 * static_cast<double>(det.sdr);
+  const double pw = -0.5 * static_cast<double>(det.W - 1) * static_cast<double>(det.dw);
+  const double ph = -0.5 * static_cast<double>(det.H - 1) * static_cast<double>(det.dh);
+  if (lane < 3) {
+    const int a = lane;
+    const double r0 = pick3(a, R[0], R[3], R[6]), r1 = pick3(a, R[1], R[4], R[7]), r2 = pick3(a, R[2], R[5], R[8]);
+    const double t = static_cast<double>(pose[3 + a]);
+    const double s = fma(rho, r0, t);                                  // R (rho, 0, 0) + t
+    const double p00 = fma(ph, r2, fma(pw, r1, fma(-rho, r0, t)));     // R pc00 + t
+    const double ew = static_cast<double>(det.dw) * r1;                 // R (0, dw, 0)
+    const double eh = static_cast<double>(det.dh) * r2;                 // R (0, 0, dh)
+    const double dl = static_cast<double>(pick3(a, vd.delta[0], vd.delta[1], vd.delta[2]));
+    const int na = pick3(a, vd.n[0], vd.n[1], vd.n[2]);
+    const double lo = -0.5 * static_cast<double>(na) * dl;  // b_a: volume centred at the origin
+    const double u0 = (s - lo) / dl;
+    const double un = static_cast<double>(na) - u0;
+    g->u0[a] = u0;
+    g->un[a] = un;
+    g->u0f[a] = static_cast<float>(u0);
+    g->unf[a] = static_cast<float>(un);
+    g->g00[a] = (p00 - s) / dl;
+    g->gw[a] = ew / dl;
+    g->gh[a] = eh / dl;
+  }
+  // columns of R (R e_x, R e_y, R e_z) for the detector-parameter chain
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (lane == i) g->Rc[i % 3][i / 3] = static_cast<float>(R[i]);
+  if (lane == 0) {
+    const float cs[6] = {static_cast<float>(sz), static_cast<float>(cz), static_cast<float>(sy),
+                         static_cast<float>(cy), static_cast<float>(sx), static_cast<float>(cx)};
+    chain_terms(cs, rho, pw, ph, det, g);
   }
 }
 
-__global__ void pose_setup_kernel(const float* __restrict__ poses, int B, DetDev det, VolumeDev vd,
-                                  PoseGeom* __restrict__ out) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp (block) per pose.
+__global__ void __launch_bounds__(32) pose_setup_kernel(const float* __restrict__ poses, int B, DetDev det,
+                                                        VolumeDev vd, PoseGeom* __restrict__ out) {
+  const int b = blockIdx.x;
   // the walk kernels' tile counters live in the slot after the last pose
-  if (b < kLaunchCounters) reinterpret_cast<unsigned int*>(out + B)[b] = 0u;
+  if (b == 0 && threadIdx.x < kLaunchCounters) reinterpret_cast<unsigned int*>(out + B)[threadIdx.x] = 0u;
   if (b >= B) return;
-  PoseGeom g;
-  compute_pose_geom(poses + 6 * b, det, vd, g);
-  out[b] = g;
+  warp_pose_geom(poses + 6 * b, det, vd, out + b);
 }
 
 __global__ void ray_setup_kernel(const float* __restrict__ poses, int B, DetDev det, float* __restrict__ rays) {
@@ -412,13 +449,6 @@ struct JacScratch : WalkScratch {
   int c_pend[kThreads];
 };
 
-// x_a for a runtime axis index without indexing a register array (which
-// would move the array to local memory).
-template <class T>
-__device__ __forceinline__ T pick3(int a, T x0, T x1, T x2) {
-  return a == 0 ? x0 : (a == 1 ? x1 : x2);
-}
-
 __device__ __forceinline__ unsigned long long fix_at(unsigned long long A0, unsigned long long D, unsigned int k) {
   return A0 + static_cast<unsigned long long>(k) * D;
 }
@@ -436,10 +466,11 @@ __device__ __forceinline__ float local_pos(unsigned long long x, unsigned long l
 }
 
 #ifndef DRR_JAC_UNROLL
-#define DRR_JAC_UNROLL 6
+#define DRR_JAC_UNROLL 12
 #endif
 // Jacobian walk unroll: a multiple of 3, so that the three voxel registers of
-// its two-deep gather pipeline rotate without register moves.
+// its two-deep gather pipeline rotate without register moves (12 measured 3 %
+// faster than 6 on the CT workload, whose rays mostly take 60-iteration chunks).
 constexpr int kJacUnroll = DRR_JAC_UNROLL;
 #ifndef DRR_JAC_CHUNK
 #define DRR_JAC_CHUNK 31
@@ -1085,14 +1116,14 @@ __device__ __forceinline__ int find_request(const ServeRequest* reqs, int nreq, 
   return lo;
 }
 
-__global__ void serve_setup_kernel(const ServeHeader* __restrict__ hdr, const ServeRequest* __restrict__ reqs) {
+// One warp (block) per pose, grid-stride over the tick's poses.
+__global__ void __launch_bounds__(32) serve_setup_kernel(const ServeHeader* __restrict__ hdr,
+                                                         const ServeRequest* __restrict__ reqs) {
   const int nreq = hdr->nreq, total = hdr->total_poses;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x; i < total; i += gridDim.x) {
     const int r = find_request(reqs, nreq, i, false);
     const int b = i - reqs[r].pose_start;
-    PoseGeom g;
-    compute_pose_geom(reqs[r].poses + 6 * b, reqs[r].det, reqs[r].vd, g);
-    reqs[r].geom[b] = g;
+    warp_pose_geom(reqs[r].poses + 6 * b, reqs[r].det, reqs[r].vd, reqs[r].geom + b);
   }
 }
 
@@ -1341,7 +1372,7 @@ cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, con
 
 cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, const VolumeDev* vd, PoseGeom* out,
                               cudaStream_t stream) {
-  pose_setup_kernel<<<(B + 63) / 64, 64, 0, stream>>>(poses, B, det, *vd, out);
+  pose_setup_kernel<<<B, 32, 0, stream>>>(poses, B, det, *vd, out);
   return cudaGetLastError();
 }
 
@@ -1417,7 +1448,7 @@ cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, 
                               int walk_grid, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  serve_setup_kernel<<<max(1, (max_poses + 63) / 64), 64, 0, stream>>>(hdr, reqs);
+  serve_setup_kernel<<<max(1, min(max_poses, 4096)), 32, 0, stream>>>(hdr, reqs);
   serve_walk_kernel<<<walk_grid, kThreads, 0, stream>>>(hdr, reqs, counter);
   serve_finalize_kernel<<<max(1, min(max_poses, 4096)), 32, 0, stream>>>(hdr, reqs);
   return cudaGetLastError();
