@@ -11,31 +11,21 @@
 
 namespace drr {
 
-// Pixel tiling of the ray kernels: a 256-thread block covers 32 x 8 pixels,
-// each warp a kWarpTileW x kWarpTileH tile (8 x 4 by default) so that its 32
-// rays are spatial neighbours and their voxel gathers share cache lines.
+// Pixel tiling of the ray kernels: the work unit is a warp tile of
+// kWarpTileW x kWarpTileH pixels (8 x 4 by default), so that a warp's 32 rays
+// are spatial neighbours and their voxel gathers share cache lines; warps of
+// 256-thread blocks claim tiles from a counter.
 #ifndef DRR_WARP_TILE_W
 #define DRR_WARP_TILE_W 8
 #endif
 constexpr int kThreads = 256;
-constexpr int kTileW = 32;
-constexpr int kTileH = 8;
 constexpr int kWarpTileW = DRR_WARP_TILE_W;
 constexpr int kWarpTileH = 32 / kWarpTileW;
-constexpr int kWarpsX = kTileW / kWarpTileW;
 static_assert(kWarpTileW >= 4 && kWarpTileW <= 32 && 32 % kWarpTileW == 0, "warp tile width");
-static_assert((kTileW / kWarpTileW) * (kTileH / kWarpTileH) == kThreads / 32, "8 warps per block tile");
 
 // Tile counters of the walk kernels, kept in the geometry buffer right after the
 // last pose's PoseGeom and zeroed by the pose-setup kernel.
 constexpr int kLaunchCounters = 4;
-
-// Pixel of thread `tid` in block tile (tx, ty).
-__host__ __device__ __forceinline__ void tile_pixel(int tx, int ty, int tid, int* h, int* w) {
-  const int lane = tid & 31, warp = tid >> 5;
-  *w = tx * kTileW + (warp % kWarpsX) * kWarpTileW + lane % kWarpTileW;
-  *h = ty * kTileH + (warp / kWarpsX) * kWarpTileH + lane / kWarpTileW;
-}
 
 enum StorageType : int { kF32 = 0, kBF16 = 1, kF16 = 2 };
 
@@ -93,8 +83,8 @@ struct ServeRequest {
   float* partials;     // [B][tiles per pose][6] (gradient requests)
   float* grad_pose;    // [B][6] (gradient requests)
   PoseGeom* geom;      // [B]
-  int B, tiles_x, tiles_y;
-  int tile_start;      // first tile of this request in the tick's global tile numbering
+  int B;
+  int tile_start;      // first warp tile of this request in the tick's global tile numbering
   int pose_start;      // first pose of this request in the tick's global pose numbering
   int pad_;
 };

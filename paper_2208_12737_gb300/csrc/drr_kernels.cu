@@ -1137,44 +1137,53 @@ __device__ __forceinline__ void serve_trace(const VolumeDev& vd, const PoseGeom&
   }
 }
 
-// Persistent walk: blocks claim 32x8-pixel tiles of any request until the
-// tick's tiles run out; render-only tiles run the forward walk, gradient
-// tiles the Jacobian walk with each warp's sum of g . J written per 8x4 tile.
+// Persistent walk: warps claim 8x4-pixel tiles of any request (numbered per
+// request as in siddon_kernel, pose-major) until the tick's tiles run out, so
+// a small request spreads over many SMs.  Render-only tiles run the forward
+// walk, gradient tiles the Jacobian walk with the warp's sum of g . J written
+// per tile; a warp copies its request's record and pose geometry to its own
+// shared slots when they change.
 __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHeader* __restrict__ hdr,
                                                                  const ServeRequest* __restrict__ reqs,
                                                                  int* __restrict__ counter) {
-  __shared__ PoseGeom spg;
-  __shared__ ServeRequest sr;
+  __shared__ PoseGeom spg[kThreads / 32];
+  __shared__ ServeRequest sreq[kThreads / 32];
   __shared__ JacScratch ws;
-  __shared__ int s_tile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nreq = hdr->nreq, total = hdr->total_tiles;
+  ServeRequest& sr = sreq[warp];
+  PoseGeom& pg = spg[warp];
+  int cur_r = -1, cur_b = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
-    __syncthreads();
-    const int t = s_tile;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);  // also: every lane is done with the previous tile
     if (t >= total) break;
     const int r = find_request(reqs, nreq, t, true);
-    {
+    if (r != cur_r) {
       const unsigned int* src = reinterpret_cast<const unsigned int*>(reqs + r);
       unsigned int* dst = reinterpret_cast<unsigned int*>(&sr);
-      for (int i = threadIdx.x; i < static_cast<int>(sizeof(ServeRequest) / 4); i += kThreads) dst[i] = src[i];
+      for (int i = lane; i < static_cast<int>(sizeof(ServeRequest) / 4); i += 32) dst[i] = src[i];
+      __syncwarp();
+      cur_r = r;
+      cur_b = -1;
     }
-    __syncthreads();
-    const int per_pose = sr.tiles_x * sr.tiles_y;
+    const int per_pose = pose_tiles(sr.det);
     const int local = t - sr.tile_start;
     const int b = local / per_pose;
+    if (b < 0 || b >= sr.B) continue;  // the tick table's tile ranges, checked (uniform in the warp)
     const int tin = local - b * per_pose;
-    const int ty = tin / sr.tiles_x, tx = tin - ty * sr.tiles_x;
-    const bool in_range = b >= 0 && b < sr.B;  // the tick table's tile ranges, checked
-    if (in_range) {
+    if (b != cur_b) {
       const unsigned int* src = reinterpret_cast<const unsigned int*>(sr.geom + b);
-      unsigned int* dst = reinterpret_cast<unsigned int*>(&spg);
-      for (int i = threadIdx.x; i < static_cast<int>(sizeof(PoseGeom) / 4); i += kThreads) dst[i] = src[i];
+      unsigned int* dst = reinterpret_cast<unsigned int*>(&pg);
+      for (int i = lane; i < static_cast<int>(sizeof(PoseGeom) / 4); i += 32) dst[i] = src[i];
+      __syncwarp();
+      cur_b = b;
     }
-    __syncthreads();
-    int h, w;
-    tile_pixel(tx, ty, threadIdx.x, &h, &w);
-    const bool valid = in_range && (w < sr.det.W) && (h < sr.det.H);
+    const int twx = (sr.det.W + kWarpTileW - 1) / kWarpTileW;
+    const int ty = tin / twx, tx = tin - ty * twx;
+    const int h = ty * kWarpTileH + lane / kWarpTileW, w = tx * kWarpTileW + lane % kWarpTileW;
+    const bool valid = (w < sr.det.W) && (h < sr.det.H);
     const size_t npix = static_cast<size_t>(sr.det.H) * sr.det.W;
     const size_t pix = static_cast<size_t>(h) * sr.det.W + w;
     const bool want_grad = sr.grad != nullptr;
@@ -1186,15 +1195,13 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
     if (valid) {
       if (want_grad) {
         gsc = sr.grad[b * npix + pix];
-        serve_trace<kPoseGrad>(sr.vd, spg, h, w, gsc, &ws, res);
+        serve_trace<kPoseGrad>(sr.vd, pg, h, w, gsc, &ws, res);
       } else {
-        serve_trace<kFwd>(sr.vd, spg, h, w, 0.f, &ws, res);
+        serve_trace<kFwd>(sr.vd, pg, h, w, 0.f, &ws, res);
       }
       sr.out[b * npix + pix] = res.F;
     }
-    if (want_grad && in_range) {  // uniform across the block
-      // one partial per 8x4 warp tile, numbered as in siddon_kernel, so that the
-      // fixed-order finalize gives the same bits as a direct render_backward
+    if (want_grad) {  // uniform across the warp: one partial per tile, as a direct render_backward
       float c[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
@@ -1202,16 +1209,12 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
       }
-      const int warp = threadIdx.x >> 5;
-      const int wtx = tx * kWarpsX + warp % kWarpsX, wty = ty * (kTileH / kWarpTileH) + warp / kWarpsX;
-      const int twx = (sr.det.W + kWarpTileW - 1) / kWarpTileW;
-      if ((threadIdx.x & 31) == 0 && wtx * kWarpTileW < sr.det.W && wty * kWarpTileH < sr.det.H) {
-        const size_t slot = static_cast<size_t>(b) * pose_tiles(sr.det) + static_cast<size_t>(wty) * twx + wtx;
+      if (lane == 0) {
+        const size_t slot = static_cast<size_t>(b) * per_pose + tin;
 #pragma unroll
         for (int k = 0; k < 6; ++k) sr.partials[slot * 6 + k] = c[k];
       }
     }
-    __syncthreads();  // shared request / pose data is rewritten for the next tile
   }
 }
 

@@ -49,7 +49,6 @@ struct Req {
   drr_request r{};
   drr::DetDev det{};
   bool grad = false;
-  int tiles_x = 0, tiles_y = 0;
   size_t npix = 0;
   size_t dev_bytes = 0, host_bytes = 0;
   size_t dev_off = 0, host_off = 0;
@@ -191,8 +190,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     Req* q = batch[i];
     q->tick = t->id;
     const size_t B = static_cast<size_t>(q->r.B);
-    const size_t nt = static_cast<size_t>(drr::pose_tiles(q->det));        // gradient partials per pose
-    const size_t nblk = static_cast<size_t>(q->tiles_x) * q->tiles_y;      // walk work tiles per pose
+    const size_t nt = static_cast<size_t>(drr::pose_tiles(q->det));  // walk tiles and gradient partials per pose
     char* d = dev_base + q->dev_off;
     char* h = host_base + q->host_off;
     q->d_poses = reinterpret_cast<float*>(d); d += up(B * 6 * 4);
@@ -220,11 +218,9 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     sr.grad_pose = q->d_gpose;
     sr.geom = q->d_geom;
     sr.B = q->r.B;
-    sr.tiles_x = q->tiles_x;
-    sr.tiles_y = q->tiles_y;
     sr.tile_start = tile_start;
     sr.pose_start = pose_start;
-    tile_start += static_cast<int>(B * nblk);
+    tile_start += static_cast<int>(B * nt);  // the walk claims 8x4 warp tiles
     pose_start += static_cast<int>(B);
   }
   hdr->nreq = static_cast<int>(batch.size());
@@ -394,10 +390,8 @@ drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* tic
   q->r = *req;
   q->det = dd;
   q->grad = req->grad_drr != nullptr;
-  q->tiles_x = (dd.W + drr::kTileW - 1) / drr::kTileW;
-  q->tiles_y = (dd.H + drr::kTileH - 1) / drr::kTileH;
   q->npix = size_t(dd.H) * dd.W;
-  if (size_t(req->B) * q->tiles_x * q->tiles_y >= (size_t(1) << 30)) {
+  if (size_t(req->B) * size_t(drr::pose_tiles(dd)) >= (size_t(1) << 30)) {
     delete q;
     return drr::set_error(DRR_ERR_INVALID, "request has too many tiles");
   }
