@@ -672,6 +672,20 @@ def run_ours(args, rank, world, local_rank):
         G_h.copy_(G, non_blocking=True)
 
     e2e_ms = timed(e2e, args.steps)
+    # the same step captured once in a CUDA graph and replayed (no host launch work per step)
+    graph_ms = None
+    try:
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph_ms = statistics.mean(timed(graph.replay, args.steps))
+    except RuntimeError as exc:  # capture refused: report the reason instead of a number
+        graph_ms = str(exc).splitlines()[0]
     torch.cuda.synchronize()
     clk = clocks.stop()
     drr.profile_reset()
@@ -712,6 +726,8 @@ def run_ours(args, rank, world, local_rank):
                      "gathered_gbs": gather_gbs},
         "e2e": {"value": job_throughput(world, rays, ems), "unit": UNIT, "h2d_bytes_per_step": B * 6 * 4,
                 "d2h_bytes_per_step": B * H * W * 4 + B * 6 * 4},
+        "graph_replay": ({"ms_per_step": graph_ms, "value": job_throughput(1, rays, graph_ms), "unit": UNIT}
+                         if isinstance(graph_ms, float) else {"unavailable": graph_ms}),
         "gpu_launches": int(launches),
         "clocks": clk,
         "wall_s_timed": wall,
