@@ -188,8 +188,10 @@ def run_reference(args, rank, world):
             base = cb
     value = statistics.median(per)
     base["value"] = value
+    rays_per_step = cfg["batch"] * cfg["detector"].height * cfg["detector"].width
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rays_per_step / (value * 1e9) * 1e3,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "volume": "512x512x133 HU->FP32", "detector": "200x200 @1.4mm",
                        "batch": cfg["batch"], "sample": base["sample"]},
