@@ -412,7 +412,7 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 #define DRR_UNROLL 8
 #endif
 #ifndef DRR_FWD_MINB
-#define DRR_FWD_MINB 5
+#define DRR_FWD_MINB 4
 #endif
 #ifndef DRR_JAC_MINB
 #define DRR_JAC_MINB 4
@@ -648,7 +648,10 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     if (p1) { g1 += wgt; h1 = fmaf(wgt, ac, h1); }         \
   }
     // The gathers run two crossings ahead: crossing m+1 (an1, q0/q1, voxel v1
-    // after it) is taken while segment m is summed.
+    // after it) is taken while segment m is summed, and a crossing's weight is
+    // taken once the voxel after it has had one walk step to arrive.  First the
+    // pending crossing at the anchor.
+    DRR_JAC_ACCOUNT()
     DRR_JAC_STEP(a1st, b1x, b1y)
     float an1 = a1st;
     bool q0 = b1x, q1 = b1y;
@@ -656,24 +659,24 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     float gmin = 3.0e38f;
 #pragma unroll kJacUnroll
     for (int m = 1; m < n; ++m) {
-      DRR_JAC_ACCOUNT()
       DRR_JAC_STEP(an2, bx, by)
       const float v2 = Voxel<DT>::load(vd.data, off);
       const float seg = an1 - ac;
       gmin = fminf(gmin, seg);
       f = fmaf(seg, v, f);
+      {  // crossing m, at the end of the segment just summed
+        const float wgt = v - v1;
+        if (q0) { g0 += wgt; h0 = fmaf(wgt, an1, h0); }
+        if (q1) { g1 += wgt; h1 = fmaf(wgt, an1, h1); }
+      }
       ac = an1;
-      p0 = q0;
-      p1 = q1;
       q0 = bx;
       q1 = by;
-      vprev = v;
       v = v1;
       v1 = v2;
       an1 = an2;
     }
-    // drain: the segment that ends at the chunk's last crossing
-    DRR_JAC_ACCOUNT()
+    // drain: the segment that ends at the chunk's last crossing, which stays pending
     {
       const float seg = an1 - ac;
       gmin = fminf(gmin, seg);
