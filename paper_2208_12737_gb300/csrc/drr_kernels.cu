@@ -398,38 +398,19 @@ __device__ __forceinline__ unsigned int hi32(unsigned long long x) { return stat
 // ---------------------------------------------------------------------------
 // Chunked walk.  The exact fixed-point crossing positions are the reference
 // frame, but the per-segment arithmetic runs in FP32 on positions measured from
-// a nearby origin: every kChunk segments the next crossing of each axis is
-// recomputed exactly (first + k * delta in 64-bit) relative to the exact
-// position of the current point, so local positions stay below ~kChunk plane
-// gaps and carry ~2^-29 of the span in absolute precision instead of the
-// 2^-24 * alpha of a whole-ray FP32 walk.  Positions are in fixed-point high-word
-// units (span / 2^29).
+// a nearby origin: at the start of every chunk of crossings the next crossing
+// of each axis is recomputed exactly (first + k * delta in 64-bit) relative to
+// the exact position of the current point, so local positions stay below
+// ~chunk plane gaps and carry ~2^-28 of the span in absolute precision instead
+// of the 2^-24 * alpha of a whole-ray FP32 walk.  Positions are in fixed-point
+// high-word units (span / 2^29).
 // ---------------------------------------------------------------------------
-#ifndef DRR_CHUNK
-#define DRR_CHUNK 32
-#endif
-#ifndef DRR_UNROLL
-#define DRR_UNROLL 8
-#endif
 #ifndef DRR_FWD_MINB
 #define DRR_FWD_MINB 4
 #endif
 #ifndef DRR_JAC_MINB
 #define DRR_JAC_MINB 4
 #endif
-// Forward walk chunk, per ray: the FP32 error of a local position grows with
-// the chunk's share of the ray (chunk / segments), so long rays take longer
-// chunks (fewer exact re-anchorings) and short rays shorter ones.  DRR_CHUNK is
-// the chunk of a ray with 256 to 512 segments; all four are multiples of the unroll.
-constexpr int kChunk = DRR_CHUNK;
-#ifndef DRR_FWD_ADAPTIVE
-#define DRR_FWD_ADAPTIVE 1
-#endif
-__device__ __forceinline__ int fwd_chunk(int nseg) {
-  return DRR_FWD_ADAPTIVE ? (nseg > 512 ? 2 * kChunk : nseg > 256 ? kChunk : nseg > 128 ? kChunk / 2 : kChunk / 4)
-                          : kChunk;
-}
-constexpr int kUnroll = DRR_UNROLL;
 constexpr float kTwoM32 = 2.3283064365386963e-10f;  // 2^-32
 
 // Per-thread exact crossing parameters, kept in shared memory: they are read
@@ -465,32 +446,29 @@ __device__ __forceinline__ float local_pos(unsigned long long x, unsigned long l
   return fix_to_float(static_cast<long long>(x - O));
 }
 
+// Both walks gather two crossings ahead: the first crossing of a chunk is
+// peeled and the unrolled loop runs chunk - 1 times.  The three voxel registers
+// of that pipeline rotate without register moves when the unroll is a multiple
+// of 3; chunk - 1 is a multiple of both unrolls.
+#ifndef DRR_FWD_UNROLL
+#define DRR_FWD_UNROLL 6
+#endif
 #ifndef DRR_JAC_UNROLL
 #define DRR_JAC_UNROLL 12
 #endif
-// Jacobian walk unroll: a multiple of 3, so that the three voxel registers of
-// its two-deep gather pipeline rotate without register moves (12 measured 3 %
-// faster than 6 on the CT workload, whose rays mostly take 60-iteration chunks).
+constexpr int kFwdUnroll = DRR_FWD_UNROLL;
 constexpr int kJacUnroll = DRR_JAC_UNROLL;
-#ifndef DRR_JAC_CHUNK
-#define DRR_JAC_CHUNK 31
-#endif
-// Jacobian chunk length: the first crossing of a chunk is peeled, so the
-// unrolled loop runs chunk - 1 times; 61, 31, 19 and 13 keep that a whole
-// number of unrolled bodies.
-constexpr int kJacChunk = DRR_JAC_CHUNK;
-#ifndef DRR_JAC_ADAPTIVE
-#define DRR_JAC_ADAPTIVE 1
-#endif
-// Jacobian chunk per ray, as for the forward walk: 6k + 1 crossings (61, 31, 19, 13).
-__device__ __forceinline__ int jac_chunk(int nseg) {
-  return DRR_JAC_ADAPTIVE ? (nseg > 512   ? 2 * kJacChunk - 1
-                             : nseg > 256 ? kJacChunk
-                             : nseg > 128 ? (kJacChunk + 7) / 2
-                                          : (kJacChunk + 7) / 2 - 6)
-                          : kJacChunk;
+// Chunk length per ray.  The FP32 error of a local position grows with the
+// chunk's share of the ray, so long rays take long chunks (fewer exact
+// re-anchorings) and short rays short ones; 6k + 1 crossings (61, 31, 19, 13).
+__device__ __forceinline__ int walk_chunk(int nseg) {
+  return nseg > 512 ? 61 : nseg > 256 ? 31 : nseg > 128 ? 19 : 13;
 }
 
+// Forward walk (Eq. 2 with the crossings of Eq. 3 taken in order, Sec. 2.2).
+// The gathers run two crossings ahead of the accumulation (the first crossing
+// of a chunk is peeled); the segment that ends at a chunk's last crossing takes
+// that crossing's exact position.
 template <int DT>
 __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetup& r, WalkScratch* ws) {
   const int t = threadIdx.x;
@@ -507,50 +485,56 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
   float v = Voxel<DT>::load(vd.data, off);
   float acc = 0.f;
   int remaining = r.nseg - 1;
-  const int chunk = fwd_chunk(r.nseg);
-  for (;;) {
+  const int chunk = walk_chunk(r.nseg);
+  while (remaining > 0) {
     const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], kx), O);
     const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], ky), O);
     const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], kz), O);
     float tx = x0, ty = y0, tz = z0;
     float lx = 0.f, ly = 0.f, lz = 0.f;
-    float ac = 0.f;
     const int n = min(remaining, chunk);
-#pragma unroll kUnroll
-    for (int m = 0; m < n; ++m) {
-      const float an = fminf(fminf(tx, ty), tz);
-      const bool bx = tx == an;
-      const bool by = !bx && ty == an;
-      const bool bz = !bx && !by;
-      off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);
-      if (bx) lx += 1.f;
-      if (by) ly += 1.f;
-      if (bz) lz += 1.f;
-      tx = fmaf(lx, dx, x0);
-      ty = fmaf(ly, dy, y0);
-      tz = fmaf(lz, dz, z0);
-      const float vn = Voxel<DT>::load(vd.data, off);
-      acc = fmaf(an - ac, v, acc);
-      ac = an;
-      v = vn;
+#define DRR_FSTEP(an)                                       \
+  const float an = fminf(fminf(tx, ty), tz);                \
+  {                                                         \
+    const bool bx = tx == an;                               \
+    const bool by = !bx && ty == an;                        \
+    const bool bz = !bx && !by;                             \
+    off += bx ? r.step[0] : (by ? r.step[1] : r.step[2]);   \
+    if (bx) lx += 1.f;                                      \
+    if (by) ly += 1.f;                                      \
+    if (bz) lz += 1.f;                                      \
+    tx = fmaf(lx, dx, x0);                                  \
+    ty = fmaf(ly, dy, y0);                                  \
+    tz = fmaf(lz, dz, z0);                                  \
+  }
+    DRR_FSTEP(a1)
+    float an1 = a1;
+    float v1 = Voxel<DT>::load(vd.data, off);
+    float ac = 0.f;
+#pragma unroll kFwdUnroll
+    for (int m = 1; m < n; ++m) {
+      DRR_FSTEP(an2)
+      const float v2 = Voxel<DT>::load(vd.data, off);
+      acc = fmaf(an1 - ac, v, acc);
+      ac = an1;
+      an1 = an2;
+      v = v1;
+      v1 = v2;
     }
+#undef DRR_FSTEP
     remaining -= n;
     kx += static_cast<unsigned int>(lx);
     ky += static_cast<unsigned int>(ly);
     kz += static_cast<unsigned int>(lz);
-    // the current point is the last crossing taken: the largest previous crossing
     unsigned long long Onew = O;
     if (kx) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], kx - 1u));
     if (ky) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], ky - 1u));
     if (kz) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], kz - 1u));
-    if (remaining == 0) {
-      acc = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O) - ac, v, acc);
-      break;
-    }
-    // keep the running sum exact across the re-anchoring: ac (local) becomes 0 at Onew
-    acc = fmaf(local_pos(Onew, O) - ac, v, acc);
+    acc = fmaf(local_pos(Onew, O) - ac, v, acc);  // the segment ending at the chunk's last crossing, exact end
+    v = v1;
     O = Onew;
   }
+  acc = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O), v, acc);
   return acc * r.unit;
 }
 
@@ -613,7 +597,7 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
   bool p0 = r.ea == a0, p1 = r.ea == a1;
   if (r.ea < 0) Gc = -v;  // entry clamped at alpha 0: weight -V_first
   int remaining = r.nseg - 1;
-  const int chunk = jac_chunk(r.nseg);
+  const int chunk = walk_chunk(r.nseg);
   while (remaining > 0) {
     const int n = min(remaining, chunk);
     ws->c_off[t] = off;
