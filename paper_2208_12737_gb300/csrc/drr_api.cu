@@ -252,7 +252,7 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
   if (!(dx_mm > 0.f && dy_mm > 0.f && dz_mm > 0.f) || !std::isfinite(dx_mm) || !std::isfinite(dy_mm) ||
       !std::isfinite(dz_mm))
     return drr::set_error(DRR_ERR_INVALID, "voxel spacing must be positive and finite");
-  const int64_t padded = int64_t(nx + 2) * (ny + 2) * (nz + 2);
+  const int64_t padded = (int64_t(nx) + 2) * (int64_t(ny) + 2) * (int64_t(nz) + 2);
   if (padded >= (int64_t{1} << 31)) return drr::set_error(DRR_ERR_INVALID, "volume too large (padded voxels >= 2^31)");
   drr_dtype storage = DRR_F32;
   float mu_water = 0.02f;

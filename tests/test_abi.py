@@ -59,3 +59,38 @@ def test_argument_errors_without_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.drr_volume_create(None, 0, 0, 1, 1, 1, ctypes.c_float(1), ctypes.c_float(1), ctypes.c_float(1),
                                  None, None, ctypes.byref(out)) == 1
+
+
+def _create(lib, data, nx, ny, nz, dx=1.0, dy=1.0, dz=1.0, src_dtype=0):
+    out = ctypes.c_void_p()
+    lib.drr_volume_create.restype = ctypes.c_int
+    lib.drr_last_error.restype = ctypes.c_char_p
+    st = lib.drr_volume_create(data, 0, src_dtype, nx, ny, nz, ctypes.c_float(dx), ctypes.c_float(dy),
+                               ctypes.c_float(dz), None, None, ctypes.byref(out))
+    return st, lib.drr_last_error().decode(), out.value
+
+
+def test_volume_limits_are_checked_before_any_device_work(lib):
+    # argument validation happens on the host before any CUDA call, so it runs here
+    buf = ctypes.create_string_buffer(64)
+    st, msg, h = _create(lib, buf, 1291, 1291, 1291)  # (n+2)^3 = 2.16e9 padded voxels >= 2^31
+    assert st == 1 and "too large" in msg and h is None
+    st, msg, _ = _create(lib, buf, 2147483646, 2, 2)  # no int32 overflow in the size check
+    assert st == 1 and "too large" in msg
+    st, msg, _ = _create(lib, buf, 0, 4, 4)
+    assert st == 1 and "positive" in msg
+    st, msg, _ = _create(lib, buf, 4, 4, 4, dx=0.0)
+    assert st == 1 and "spacing" in msg
+    st, msg, _ = _create(lib, buf, 4, 4, 4, dz=float("inf"))
+    assert st == 1 and "spacing" in msg
+    st, msg, _ = _create(lib, None, 4, 4, 4)
+    assert st == 1 and "NULL" in msg
+    st, msg, _ = _create(lib, buf, 4, 4, 4, src_dtype=1)  # BF16 is a storage type, not an input type
+    assert st == 1 and "src_dtype" in msg
+
+
+def test_calls_on_a_null_volume_fail_cleanly(lib):
+    lib.drr_render.restype = ctypes.c_int
+    lib.drr_last_error.restype = ctypes.c_char_p
+    st = lib.drr_render(None, None, None, 1, None, None, None)
+    assert st == 1 and b"NULL" in lib.drr_last_error()
