@@ -125,7 +125,7 @@ drr_status drr_render(drr_volume v, const drr_detector* det, const float* poses_
  *                    rays and form the Jacobian on the fly.
  *  grad_pose_dev   : NULL, or [B][6] float32, overwritten with
  *                    sum_{h,w} dL/dE(h,w) dE(h,w)/d eta (deterministic:
- *                    fixed-order reduction, FP64 second pass).
+ *                    fixed-order reduction, FP64 across threads and blocks).
  *  grad_volume_dev : NULL, or [nz][ny][nx] float32 dL/dV (attenuation units),
  *                    ACCUMULATED into (back-projection with atomic adds; the
  *                    summation order, hence the last bits, is not deterministic).
@@ -141,17 +141,11 @@ drr_status drr_render_backward(drr_volume v, const drr_detector* det, const floa
  * device-memory footprint up front and forbids later allocations, or a plugin
  * whose host framework owns every device allocation.
  *  det, B, grad_drr_dev, jac_dev, grad_pose_dev: as for drr_render_backward with
- *  a stored Jacobian and grad_volume_dev == NULL; the result is the same.
- * The per-block partial sums live in one fixed array of device memory inside the
- * library (1 MiB per GPU, held by every GPU that loads the library until the
- * process exits), so B * ceil(H*W / 2048) * 6 must not exceed 262144; larger
- * requests are rejected with DRR_ERR_INVALID and a message naming the limit.
- * The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before capturing a
- * stream.  Every call uses the same array: calls whose work can overlap on the
- * GPU (different streams without ordering between them) race and corrupt each
- * other's results, so serialise them.  Nothing in the array needs clearing
- * between calls: every partial sum is written before it is read. */
+ *  a stored Jacobian and grad_volume_dev == NULL; the result is bitwise the same
+ *  (the same single launch: one thread-block cluster per pose keeps every
+ *  partial sum on chip, so no scratch memory is involved and calls on any
+ *  streams may overlap).  Errors: DRR_ERR_INVALID (sizes, NULL pointers),
+ *  DRR_ERR_CUDA (launch). */
 drr_status drr_pose_grad_noalloc(const drr_detector* det, int32_t B, const float* grad_drr_dev,
                                  const float* jac_dev, float* grad_pose_dev, void* cuda_stream);
 

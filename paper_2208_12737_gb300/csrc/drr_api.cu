@@ -428,14 +428,17 @@ drr_status drr_render_backward(drr_volume v, const drr_detector* det, const floa
   if (need_geom) {
     if (drr_status s = setup_geometry(v, dd, poses_dev, B, st, pg)) return s;
   }
-  if (grad_pose_dev) {
-    const int nblk = drr::pose_grad_blocks(dd, jac_dev != nullptr);
+  if (grad_pose_dev && jac_dev) {
+    LaunchScope ls(kJacReduce, st);
+    DRR_CUDA(drr::launch_pose_grad_from_jacobian(dd, B, grad_drr_dev, jac_dev, grad_pose_dev, st),
+             "pose-gradient launch");
+  } else if (grad_pose_dev) {
+    const int nblk = drr::pose_tiles(dd);
     AsyncBuf<float> partials;
     DRR_CUDA(partials.alloc(size_t(B) * nblk * 6, st), "cudaMallocAsync(pose-gradient partials)");
     {
-      LaunchScope ls(jac_dev ? kJacReduce : kSiddonPoseGrad, st);
-      DRR_CUDA(drr::launch_pose_grad_partials(v->vd, dd, pg.p, B, grad_drr_dev, jac_dev, partials.p, st),
-               "pose-gradient launch");
+      LaunchScope ls(kSiddonPoseGrad, st);
+      DRR_CUDA(drr::launch_pose_grad_walk(v->vd, dd, pg.p, B, grad_drr_dev, partials.p, st), "pose-gradient launch");
     }
     LaunchScope ls(kFinalize, st);
     DRR_CUDA(drr::launch_pose_grad_finalize(partials.p, B, nblk, grad_pose_dev, st), "pose-gradient finalize");

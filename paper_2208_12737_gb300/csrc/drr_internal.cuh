@@ -103,7 +103,6 @@ cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, cons
 cudaError_t launch_ray_setup(const float* poses, int B, const DetDev& det, float* rays, cudaStream_t stream);
 cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
                           cudaStream_t stream);
-// Pose gradient by re-tracing (jac == nullptr) or from a stored Jacobian.
 // Comparison baseline: the plain FP32 forward walk (out: [B][H][W]).
 cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out,
                                      cudaStream_t stream);
@@ -111,18 +110,20 @@ cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, con
 // apart (0: one fixed image for all), and optionally d loss / d moving.
 cudaError_t launch_zncc(const float* moving, const float* fixed, size_t fixed_stride, int B, int npix, float eps,
                         float* loss, float* grad, cudaStream_t stream);
-// partials must hold B * pose_grad_blocks(det) * 6 floats.
-int pose_grad_blocks(const DetDev& det, bool from_jacobian);
-cudaError_t launch_pose_grad_partials(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
-                                      const float* grad_drr, const float* jac, float* partials, cudaStream_t stream);
+// Pose gradient by re-tracing: one partial sum of g . J per warp tile
+// (partials: B * pose_tiles(det) * 6 floats), then the fixed-order FP64
+// finalize over nblk = pose_tiles(det) partials per pose.
+cudaError_t launch_pose_grad_walk(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
+                                  const float* grad_drr, float* partials, cudaStream_t stream);
 cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream);
+// Pose gradient from a stored Jacobian [B][6][H][W]: one launch, no scratch
+// memory (one thread-block cluster per pose), grad_pose [B][6] overwritten.
+cudaError_t launch_pose_grad_from_jacobian(const DetDev& det, int B, const float* grad_drr, const float* jac,
+                                           float* grad_pose, cudaStream_t stream);
 // dL/d(sdr, dh, dw) per pose by a re-walk: partials must hold
 // B * pose_tiles(det) * 3 floats; grad_geometry is [B][3].
 cudaError_t launch_geometry_grad(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
                                  const float* grad_drr, float* partials, float* grad_geometry, cudaStream_t stream);
-// The stored-Jacobian half of launch_pose_grad_partials on its own.
-cudaError_t launch_jac_reduce(const DetDev& det, int B, const float* grad_drr, const float* jac, float* partials,
-                              cudaStream_t stream);
 cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, int* counts,
                                   cudaStream_t stream);
 cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,

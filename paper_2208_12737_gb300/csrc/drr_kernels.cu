@@ -10,7 +10,9 @@
 //   Sec. 2.3 entry/exit clip a_min / a_max
 //   Sec. 2.4 pose parameterisation and differentiation w.r.t. the pose
 #include <algorithm>
+#include <cstdint>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -50,11 +52,21 @@ __device__ __forceinline__ T pick3(int a, T x0, T x1, T x2) {
   return a == 0 ? x0 : (a == 1 ? x1 : x2);
 }
 
+// Programmatic dependent launch (sm_90 and later).  The pose-setup, walk and
+// gradient-reduction kernels are launched with programmatic stream
+// serialization, so each can be scheduled while the kernel before it in the
+// stream is still finishing.  grid_dep_wait() blocks until that kernel has
+// completed and its writes are visible; each of these kernels calls it before
+// its first global-memory access (read or write).  grid_dep_release() lets the
+// next kernel in the stream be scheduled early; its blocks then wait in their
+// own grid_dep_wait().  Both are no-ops for a kernel launched without the
+// attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // ---------------------------------------------------------------------------
 // Pose -> frame (Sec. 2.4).  R = Rz(eta0) Ry(eta1) Rx(eta2).
 // ---------------------------------------------------------------------------
-// World-space frame of one pose: source s, pixel (0,0) centre p00, the
-// per-column and per-row pixel steps ew, eh, and optionally dR/d eta_j.
 // World-space frame of one pose: source s, pixel (0,0) centre p00, the
 // per-column and per-row pixel steps ew, eh (all FP64), and optionally R and
 // the sines / cosines of the three angles.  R = Rz Ry Rx written out.
@@ -198,6 +210,8 @@ __device__ void warp_pose_geom(const float* pose, const DetDev& det, const Volum
 // One warp (block) per pose.
 __global__ void __launch_bounds__(32) pose_setup_kernel(const float* __restrict__ poses, int B, DetDev det,
                                                         VolumeDev vd, PoseGeom* __restrict__ out) {
+  grid_dep_wait();
+  grid_dep_release();
   const int b = blockIdx.x;
   // the walk kernels' tile counters live in the slot after the last pose
   if (b == 0 && threadIdx.x < kLaunchCounters) reinterpret_cast<unsigned int*>(out + B)[threadIdx.x] = 0u;
@@ -230,29 +244,6 @@ struct RayResult {
   float J[6];  // dE/d eta (only for the Jacobian modes)
   int nseg;    // number of segments (0 for a miss)
 };
-
-// Block-wide sum of 6 floats per thread; thread 0 gets the totals.
-__device__ __forceinline__ void block_sum6(float v[6], float (*sm)[6]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) sm[warp][k] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      float t = 0.f;
-      for (int q = 0; q < kThreads / 32; ++q) t += sm[q][k];
-      v[k] = t;
-    }
-  }
-}
 
 // Per-ray state after the FP64 setup: everything the walk needs.
 //
@@ -943,6 +934,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
                   float* __restrict__ partials, float* __restrict__ gvol) {
   __shared__ PoseGeom spg[kThreads / 32];
   __shared__ typename ScratchFor<MODE>::type ws;
+  grid_dep_wait();
+  grid_dep_release();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int twx = (det.W + kWarpTileW - 1) / kWarpTileW;
   const int per_pose = twx * ((det.H + kWarpTileH - 1) / kWarpTileH);
@@ -1006,33 +999,100 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
   }
 }
 
-// Pose gradient from a stored Jacobian: sum g * J over each chunk of pixels.
-constexpr int kJacPixPerThread = 8;
-__global__ void __launch_bounds__(kThreads) jac_reduce_kernel(const float* __restrict__ gin,
-                                                              const float* __restrict__ jac, int npix,
-                                                              float* __restrict__ partials) {
-  __shared__ float red[kThreads / 32][6];
-  const int b = blockIdx.y;
-  float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int base = blockIdx.x * (kThreads * kJacPixPerThread);
-  for (int i = 0; i < kJacPixPerThread; ++i) {
-    const int p = base + i * kThreads + threadIdx.x;
-    if (p < npix) {
-      const float gv = __ldg(gin + static_cast<size_t>(b) * npix + p);
+// Pose gradient from a stored Jacobian in one launch (Sec. 2.4, chain rule:
+// dL/d eta = sum over pixels of dL/dE * dE/d eta).  One thread-block cluster
+// per pose: block r of the cluster sums g * J over the r-th of kJacCluster
+// contiguous shares of the pose's pixels (in FP32: FP64 arithmetic is narrow
+// on this GPU), writes its six sums into a row of block 0's shared memory
+// through the cluster's distributed shared memory, and block 0 adds the rows
+// in rank order in FP64.  Every sum has a fixed order, so the result is
+// bitwise reproducible, and no partial sums leave the chip.
+constexpr int kJacCluster = 8;     // blocks per pose (the portable cluster size)
+constexpr int kJacThreads = 1024;  // enough loads in flight per SM for an HBM-rate pass
+
+__device__ __forceinline__ void jac_fma4(float c[6], const float4 gv, const float* __restrict__ jb, int npix, int i) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) c[k] = fmaf(gv, __ldg(jac + (static_cast<size_t>(b) * 6 + k) * npix + p), c[k]);
+  for (int k = 0; k < 6; ++k) {
+    const float4 jv = __ldcs(reinterpret_cast<const float4*>(jb + static_cast<size_t>(k) * npix) + i);
+    c[k] = fmaf(gv.x, jv.x, c[k]);
+    c[k] = fmaf(gv.y, jv.y, c[k]);
+    c[k] = fmaf(gv.z, jv.z, c[k]);
+    c[k] = fmaf(gv.w, jv.w, c[k]);
+  }
+}
+
+__global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(kJacThreads)
+    jac_grad_kernel(const float* __restrict__ gin, const float* __restrict__ jac, int npix, int vec,
+                    float* __restrict__ grad) {
+  static_assert(kJacThreads == 32 * 32, "the block sum takes one warp sum per lane");
+  __shared__ float wsum[kJacThreads / 32][6];
+  __shared__ double rows[kJacCluster][6];  // filled in block 0 only
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned int rank = cluster.block_rank();
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  grid_dep_wait();
+  grid_dep_release();
+  const float* gb = gin + static_cast<size_t>(b) * npix;
+  const float* jb = jac + static_cast<size_t>(b) * 6 * npix;
+  float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (vec) {  // npix % 4 == 0 and 16-byte aligned planes: float4 loads
+    const int nv = npix >> 2;
+    const int lo = static_cast<int>(static_cast<int64_t>(nv) * rank / kJacCluster);
+    const int hi = static_cast<int>(static_cast<int64_t>(nv) * (rank + 1) / kJacCluster);
+#pragma unroll 1
+    for (int i = lo + threadIdx.x; i < hi; i += kJacThreads)
+      jac_fma4(c, __ldcs(reinterpret_cast<const float4*>(gb) + i), jb, npix, i);
+  } else {
+    const int lo = static_cast<int>(static_cast<int64_t>(npix) * rank / kJacCluster);
+    const int hi = static_cast<int>(static_cast<int64_t>(npix) * (rank + 1) / kJacCluster);
+#pragma unroll 1
+    for (int p = lo + threadIdx.x; p < hi; p += kJacThreads) {
+      const float gv = __ldcs(gb + p);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) c[k] = fmaf(gv, __ldcs(jb + static_cast<size_t>(k) * npix + p), c[k]);
     }
   }
-  block_sum6(c, red);
-  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) partials[(static_cast<size_t>(b) * gridDim.x + blockIdx.x) * 6 + k] = c[k];
+  for (int k = 0; k < 6; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) wsum[warp][k] = c[k];
+  }
+  __syncthreads();
+  // every block of the cluster is running (its shared memory exists) before any
+  // block writes into block 0's
+  cluster.sync();
+  if (warp == 0) {  // lane q holds warp q's sums; a fixed butterfly adds them
+    float t[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      t[k] = wsum[lane][k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+    }
+    float mine = t[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k)
+      if (lane == k) mine = t[k];
+    if (lane < 6) cluster.map_shared_rank(&rows[0][0], 0)[rank * 6 + lane] = static_cast<double>(mine);
+  }
+  cluster.sync();  // rows complete; no block exits while its row is still being written
+  if (rank == 0 && threadIdx.x < 6) {
+    double t = 0.0;
+    for (int r = 0; r < kJacCluster; ++r) t += rows[r][threadIdx.x];
+    grad[6 * b + threadIdx.x] = static_cast<float>(t);
   }
 }
 
 // Fixed-order FP64 sum of the per-block partials: one warp per pose.
 __global__ void pose_grad_finalize_kernel(const float* __restrict__ partials, int nblk, int ncol,
                                           float* __restrict__ grad) {
+  grid_dep_wait();
   const int b = blockIdx.x, lane = threadIdx.x;
   for (int k = 0; k < ncol; ++k) {
     double s = 0.0;
@@ -1225,6 +1285,26 @@ __global__ void serve_finalize_kernel(const ServeHeader* __restrict__ hdr, const
   }
 }
 
+// Launch with programmatic stream serialization (the kernel must begin with
+// grid_dep_wait()); -DDRR_PDL=0 launches plainly.
+#ifndef DRR_PDL
+#define DRR_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = DRR_PDL ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   if (g > 152 * 64) g = 152 * 64;
@@ -1254,8 +1334,8 @@ cudaError_t launch_siddon_dt(const VolumeDev& vd, const DetDev& det, const PoseG
   const int64_t tiles = static_cast<int64_t>(pose_tiles(det)) * B;
   const int64_t want = (tiles + kThreads / 32 - 1) / (kThreads / 32);
   const int grid = static_cast<int>(std::min<int64_t>(want, resident_blocks<MODE, DT>()));
-  siddon_kernel<MODE, DT><<<grid, kThreads, 0, stream>>>(vd, det, pg, B, counter, out, jac, gin, partials, gvol);
-  return cudaGetLastError();
+  return launch_pdl(siddon_kernel<MODE, DT>, dim3(grid), dim3(kThreads), stream, vd, det, pg, B, counter, out, jac, gin,
+                    partials, gvol);
 }
 
 template <int MODE>
@@ -1362,8 +1442,7 @@ cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, con
 
 cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, const VolumeDev* vd, PoseGeom* out,
                               cudaStream_t stream) {
-  pose_setup_kernel<<<B, 32, 0, stream>>>(poses, B, det, *vd, out);
-  return cudaGetLastError();
+  return launch_pdl(pose_setup_kernel, dim3(B), dim3(32), stream, poses, B, det, *vd, out);
 }
 
 cudaError_t launch_ray_setup(const float* poses, int B, const DetDev& det, float* rays, cudaStream_t stream) {
@@ -1378,22 +1457,18 @@ cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom
   return launch_siddon<kFwd>(vd, det, pg, B, out, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
-int pose_grad_blocks(const DetDev& det, bool from_jacobian) {
-  if (from_jacobian) {
-    const int npix = det.H * det.W;
-    return (npix + kThreads * kJacPixPerThread - 1) / (kThreads * kJacPixPerThread);
-  }
-  return pose_tiles(det);
+cudaError_t launch_pose_grad_walk(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
+                                  const float* grad_drr, float* partials, cudaStream_t stream) {
+  return launch_siddon<kPoseGrad>(vd, det, pg, B, nullptr, nullptr, grad_drr, partials, nullptr, stream);
 }
 
-cudaError_t launch_pose_grad_partials(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
-                                      const float* grad_drr, const float* jac, float* partials, cudaStream_t stream) {
-  if (jac) {
-    dim3 grid(pose_grad_blocks(det, true), B);
-    jac_reduce_kernel<<<grid, kThreads, 0, stream>>>(grad_drr, jac, det.H * det.W, partials);
-    return cudaGetLastError();
-  }
-  return launch_siddon<kPoseGrad>(vd, det, pg, B, nullptr, nullptr, grad_drr, partials, nullptr, stream);
+cudaError_t launch_pose_grad_from_jacobian(const DetDev& det, int B, const float* grad_drr, const float* jac,
+                                           float* grad_pose, cudaStream_t stream) {
+  const int npix = det.H * det.W;
+  const int vec = (npix % 4 == 0) && (reinterpret_cast<uintptr_t>(grad_drr) % 16 == 0) &&
+                  (reinterpret_cast<uintptr_t>(jac) % 16 == 0);
+  return launch_pdl(jac_grad_kernel, dim3(kJacCluster, B), dim3(kJacThreads), stream, grad_drr, jac, npix, vec,
+                    grad_pose);
 }
 
 cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, int* counts,
@@ -1402,24 +1477,16 @@ cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const 
                                stream);
 }
 
-cudaError_t launch_jac_reduce(const DetDev& det, int B, const float* grad_drr, const float* jac, float* partials,
-                              cudaStream_t stream) {
-  dim3 grid(pose_grad_blocks(det, true), B);
-  jac_reduce_kernel<<<grid, kThreads, 0, stream>>>(grad_drr, jac, det.H * det.W, partials);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream) {
-  pose_grad_finalize_kernel<<<B, 32, 0, stream>>>(partials, nblk, 6, grad_pose);
-  return cudaGetLastError();
+  return launch_pdl(pose_grad_finalize_kernel, dim3(B), dim3(32), stream, partials, nblk, 6, grad_pose);
 }
 
 cudaError_t launch_geometry_grad(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
                                  const float* grad_drr, float* partials, float* grad_geometry, cudaStream_t stream) {
   cudaError_t e = launch_siddon<kGeoGrad>(vd, det, pg, B, nullptr, nullptr, grad_drr, partials, nullptr, stream);
   if (e != cudaSuccess) return e;
-  pose_grad_finalize_kernel<<<B, 32, 0, stream>>>(partials, pose_tiles(det), 3, grad_geometry);
-  return cudaGetLastError();
+  return launch_pdl(pose_grad_finalize_kernel, dim3(B), dim3(32), stream, static_cast<const float*>(partials),
+                    pose_tiles(det), 3, grad_geometry);
 }
 
 cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,

@@ -49,10 +49,36 @@ def test_noalloc_pose_grad_matches_allocating_path(drr):
         assert grad_err(got, ref).max() < GRAD_TOL
 
 
-def test_noalloc_rejects_batches_beyond_its_scratch(drr):
-    det = inputs.Detector(300.0, 512, 512, 1.0, 1.0)  # 128 blocks per pose -> B <= 341
-    B = 400
-    g = torch.zeros((1,), device="cuda")
-    st = _call(drr, det, g.expand(B), g, g)
-    assert st == 1  # DRR_ERR_INVALID
-    assert b"scratch" in drr.load().drr_last_error()
+def _ref_grad(g, J):
+    """sum over pixels of g * J per pose and parameter, in float64 (torch on the GPU)."""
+    return (g.double().unsqueeze(1) * J.double()).sum(dim=(2, 3)).cpu().numpy()
+
+
+@pytest.mark.parametrize("B,H,W,shift", [
+    (65535, 8, 8, 0),     # the largest batch; float4 path (H*W % 4 == 0, aligned)
+    (5, 37, 53, 0),       # H*W odd: scalar path
+    (3, 64, 64, 1),       # planes offset by one float: not 16-byte aligned, scalar path
+    (2, 1024, 1024, 0),   # one cluster per pose over 1 M pixels
+])
+def test_stored_jacobian_reduction_against_float64(drr, B, H, W, shift):
+    gen = torch.Generator(device="cuda").manual_seed(B * 7 + H)
+    n = B * H * W
+    gbuf = torch.rand(n + shift, device="cuda", generator=gen) * 2 - 1
+    jbuf = torch.randn(6 * n + shift, device="cuda", generator=gen)
+    g = gbuf[shift:].view(B, H, W)
+    J = jbuf[shift:].view(B, 6, H, W)
+    out = torch.full((B, 6), float("nan"), device="cuda")
+    det = inputs.Detector(300.0, H, W, 1.0, 1.0)
+    assert _call(drr, det, g, J, out) == 0, drr.load().drr_last_error()
+    ref = _ref_grad(g, J)
+    got = out.cpu().numpy().astype(np.float64)
+    # FP32 products summed in FP32 by each thread (n terms at most), then a
+    # 10-level FP32 tree over the block's 1024 threads, FP64 across blocks: the
+    # error is below (n + 11) * 2^-24 * sum |g J| (recursive-summation bound)
+    n_per_thread = -(-(H * W) // (8 * 1024)) + 4
+    scale = (g.double().abs().unsqueeze(1) * J.double().abs()).sum(dim=(2, 3)).cpu().numpy()
+    assert np.all(np.abs(got - ref) <= (n_per_thread + 11) * 2.0**-24 * scale + 1e-30)
+    # bitwise reproducible
+    out2 = torch.empty_like(out)
+    assert _call(drr, det, g, J, out2) == 0
+    assert torch.equal(out, out2)
