@@ -248,12 +248,14 @@ struct RayResult {
 // Per-ray state after the FP64 setup: everything the walk needs.
 //
 // Crossing parameters are fixed point: alpha measured from the entry is held
-// as a 32.32 number in units of span / 2^29 (span = alpha_max - alpha_min), so
-// the high word of every crossing inside the ray lies in [0, 2^29] and the
-// exit is exactly 2^29; every value the walk forms stays below 2^62.  Each axis' crossings form the arithmetic sequence
-// first + k * delta (Eq. 3), advanced by exact 64-bit additions: ordering is
-// exact to 2^-62 of the span and segment lengths are exact integers, so the
-// FP32 arithmetic is confined to the accumulation of length x density.
+// as a 32.32 number in units of span / 2^24 (span = alpha_max - alpha_min), so
+// the high word of every crossing inside the ray lies in [0, 2^24] and the
+// exit is exactly 2^24; every value the walk forms stays below 2^58.  Each
+// axis' crossings form the arithmetic sequence first + k * delta (Eq. 3),
+// advanced by exact 64-bit additions: ordering is exact to 2^-56 of the span
+// and segment lengths are exact integers, so the FP32 arithmetic is confined
+// to the accumulation of length x density.  (A high word below 2^24 converts
+// to FP32 exactly; see fix_to_float.)
 struct RaySetup {
   int nseg;                  // segments = plane crossings + 1 (0: the ray misses)
   int off;                   // element offset of the entry voxel (padded layout)
@@ -263,14 +265,15 @@ struct RaySetup {
   int ea, xa;                // axis of the entry / exit plane, -1 when clamped to alpha = 0 / 1
   unsigned long long A0[3];  // first crossing per axis (32.32 fixed point)
   unsigned long long D[3];   // fixed-point distance between consecutive planes
-  float unit;                // alpha per fixed-point unit: span / 2^30
+  float unit;                // alpha per high-word unit: span / 2^24
   double amin;               // absolute alpha of the entry
   float d[3];                // p - s in mm
 };
 
-constexpr unsigned int kExitUnits = 1u << 29;              // the exit, in high-word units
-constexpr unsigned long long kNoCrossing64 = 1ull << 62;  // beyond any crossing of the ray
-constexpr double kFixScale = 2305843009213693952.0;        // 2^61: fixed-point value of alpha = span
+constexpr unsigned int kExitUnits = 1u << 24;              // the exit, in high-word units
+constexpr unsigned long long kFixMax = 1ull << 56;         // fixed-point value of the exit
+constexpr unsigned long long kNoCrossing64 = 1ull << 58;  // beyond any crossing of the ray
+constexpr double kFixScale = 72057594037927936.0;          // 2^56: fixed-point value of alpha = span
 
 // Reciprocal of a double to ~1e-14 relative: an FP32 seed refined by one FP64
 // Newton step (a full FP64 division costs several times more on the FP64 pipe,
@@ -373,10 +376,10 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
     const double plane = static_cast<double>(up ? i0 + 1 : i0);
     // first crossing, kept within [0, span] (rounding can put it a hair outside)
     const double f = fmax((plane - ue) * rg[a], 0.0);
-    r.A0[a] = r.cnt[a] > 0 ? min(__double2ull_rz(f * to_fix), 1ull << 61) : kNoCrossing64;
+    r.A0[a] = r.cnt[a] > 0 ? min(__double2ull_rz(f * to_fix), kFixMax) : kNoCrossing64;
     // plane spacing, saturated at the span: an axis whose planes are farther
-    // apart has at most one crossing, and one step past it stays below 2^62
-    r.D[a] = min(__double2ull_rz(fabs(rg[a]) * to_fix), 1ull << 61);
+    // apart has at most one crossing, and one step past it stays below 2^57
+    r.D[a] = min(__double2ull_rz(fabs(rg[a]) * to_fix), kFixMax);
     r.step[a] = up ? vd.stride[a] : -vd.stride[a];
   }
   r.nseg = total + 1;
@@ -384,17 +387,15 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
   return 1;
 }
 
-__device__ __forceinline__ unsigned int hi32(unsigned long long x) { return static_cast<unsigned int>(x >> 32); }
-
 // ---------------------------------------------------------------------------
 // Chunked walk.  The exact fixed-point crossing positions are the reference
 // frame, but the per-segment arithmetic runs in FP32 on positions measured from
 // a nearby origin: at the start of every chunk of crossings the next crossing
 // of each axis is recomputed exactly (first + k * delta in 64-bit) relative to
 // the exact position of the current point, so local positions stay below
-// ~chunk plane gaps and carry ~2^-28 of the span in absolute precision instead
-// of the 2^-24 * alpha of a whole-ray FP32 walk.  Positions are in fixed-point
-// high-word units (span / 2^29).
+// ~chunk plane gaps and carry 2^-24 of the chunk instead of 2^-24 of the ray's
+// alpha as a whole-ray FP32 walk would.  Positions are in fixed-point
+// high-word units (span / 2^24).
 // ---------------------------------------------------------------------------
 #ifndef DRR_FWD_MINB
 #define DRR_FWD_MINB 4
@@ -425,9 +426,11 @@ __device__ __forceinline__ unsigned long long fix_at(unsigned long long A0, unsi
   return A0 + static_cast<unsigned long long>(k) * D;
 }
 
-// FP32 value (high-word units) of a signed 32.32 fixed-point number below 2^62
-// in magnitude, from two 32-bit conversions (a 64-bit conversion would run on
-// the FP64 pipe, which is narrow on this GPU).
+// FP32 value (high-word units) of a signed 32.32 fixed-point number, from two
+// 32-bit conversions (a 64-bit conversion would run on the FP64 pipe, which is
+// narrow on this GPU).  For |d| < 2^56 -- every position within a ray, every
+// plane spacing -- the high word converts exactly, so the result carries one
+// rounding (2^-24 relative) plus at most 2^-25 units from the low word.
 __device__ __forceinline__ float fix_to_float(long long d) {
   return fmaf(static_cast<float>(static_cast<unsigned int>(d)), kTwoM32, static_cast<float>(static_cast<int>(d >> 32)));
 }
@@ -538,13 +541,16 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
 // kept in Gc, Ac).
 //
 // The order of two crossings decides the voxel between them and hence both
-// weights, so it must be exact.  The FP32 walk of a chunk can only misorder
-// two crossings whose local positions lie within their rounding error
-// (<= 1.5 * 2^-23 of the position each), and then the walk takes a segment
-// shorter than that bound at the misordered pair.  So each chunk tracks its
-// shortest segment and the gap to the next crossing after it; if either is
-// below kTieRel * position + kTieAbs, the chunk is walked again from its saved
-// start state in exact fixed-point order (rare: a few chunks per thousand).
+// weights, so it must be exact.  A chunk's FP32 position t = l * dl + x0 (x0
+// and dl each one rounding from exact values, see fix_to_float, then the FMA)
+// is within 2^-24 (x0 + l dl + t) + (l + 1) 2^-25 = 2^-23 t + (l + 1) 2^-25
+// units of the exact one, so the walk can only misorder two crossings less
+// than 2^-22 t + 62 * 2^-24 apart, and then it takes a segment no longer than
+// that at the misordered pair.  So each chunk tracks its shortest segment and
+// the gap to the next crossing after it; if either is below kTieRel * position
+// + kTieAbs (25 % and ~250x above those two terms), the chunk is walked again
+// from its saved start state in exact fixed-point order (rare: about one lane
+// in two thousand chunks).
 // Sums are kept per chunk in local positions and moved to the anchor frame
 // when the chunk ends, so a re-walk only discards the chunk's own sums.
 struct JacSums {
@@ -552,8 +558,8 @@ struct JacSums {
   int dom;
 };
 
-constexpr float kTieRel = 4.76837158203125e-7f;  // 2^-21 > twice 1.5 * 2^-23
-constexpr float kTieAbs = 4.f;                   // high-word units
+constexpr float kTieRel = 2.98023223876953125e-7f;  // 1.25 * 2^-22
+constexpr float kTieAbs = 9.765625e-4f;             // 2^-10 high-word units
 
 template <int DT>
 __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, JacScratch* ws,
@@ -669,7 +675,9 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     // the next crossing after it.
     const float next = fminf(fminf(tx, ty), tz);
     if (gmin < fmaf(ac, kTieRel, kTieAbs) || (remaining > n && next - ac < fmaf(next, kTieRel, kTieAbs))) {
-      // exact re-walk of the chunk: candidates compared as 64-bit fixed point
+      // exact re-walk of the chunk: the next crossing of each slot held as 64-bit
+      // fixed point (all ones once the slot's crossings are used up), the
+      // smallest taken each step (ties to the lower slot)
       off = ws->c_off[t];
       v = ws->c_v[t];
       vprev = ws->c_vprev[t];
@@ -678,23 +686,32 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
       p1 = pend == 1;
       ac = f = g0 = g1 = h0 = h1 = 0.f;
       c0 = c1 = c2 = 0u;
+      int r0 = ws->cnt[0][t] - static_cast<int>(k0), r1 = ws->cnt[1][t] - static_cast<int>(k1),
+          r2 = ws->cnt[2][t] - static_cast<int>(k2);
+      unsigned long long e0 = r0 > 0 ? fix_at(ws->A0[0][t], ws->D[0][t], k0) : ~0ull;
+      unsigned long long e1 = r1 > 0 ? fix_at(ws->A0[1][t], ws->D[1][t], k1) : ~0ull;
+      unsigned long long e2 = r2 > 0 ? fix_at(ws->A0[2][t], ws->D[2][t], k2) : ~0ull;
       for (int m = 0; m < n; ++m) {
         DRR_JAC_ACCOUNT()
-        const unsigned int kk[3] = {k0 + c0, k1 + c1, k2 + c2};
-        unsigned long long best = ~0ull;
-        int sel = 2;
-#pragma unroll
-        for (int sl = 0; sl < 3; ++sl) {
-          if (static_cast<int>(kk[sl]) < ws->cnt[sl][t]) {
-            const unsigned long long e = fix_at(ws->A0[sl][t], ws->D[sl][t], kk[sl]);
-            if (e < best) { best = e; sel = sl; }
-          }
+        const bool sx = e0 <= e1 && e0 <= e2;
+        const bool sy = !sx && e1 <= e2;
+        unsigned long long best;
+        if (sx) {
+          best = e0;
+          off += step[0];
+          ++c0;
+          e0 = --r0 > 0 ? e0 + ws->D[0][t] : ~0ull;
+        } else if (sy) {
+          best = e1;
+          off += step[1];
+          ++c1;
+          e1 = --r1 > 0 ? e1 + ws->D[1][t] : ~0ull;
+        } else {
+          best = e2;
+          off += step[2];
+          ++c2;
+          e2 = --r2 > 0 ? e2 + ws->D[2][t] : ~0ull;
         }
-        const bool sx = sel == 0, sy = sel == 1;
-        off += sx ? step[0] : (sy ? step[1] : step[2]);
-        c0 += sx ? 1u : 0u;
-        c1 += sy ? 1u : 0u;
-        c2 += (!sx && !sy) ? 1u : 0u;
         const float an = local_pos(best, O);
         const float vn = Voxel<DT>::load(vd.data, off);
         f = fmaf(an - ac, v, f);
@@ -838,7 +855,9 @@ __device__ __forceinline__ void geometry_jacobian(const RaySetup& r, const JacSu
 }
 
 // Back-projection walk: grad_V[voxel] += g L (a_{m+1} - a_m), the transpose of
-// the forward map V -> E; into an unpadded (nz, ny, nx) FP32 volume.
+// the forward map V -> E; into an unpadded (nz, ny, nx) FP32 volume.  Segment
+// lengths are exact integers in units of span / 2^29 (bits 27..58 of the fixed
+// point).
 __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RaySetup& r, float gL,
                                                  float* __restrict__ gvol) {
   unsigned long long Ax = r.A0[0], Ay = r.A0[1], Az = r.A0[2];
@@ -847,10 +866,13 @@ __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RayS
   const int lz = r.step[2] > 0 ? vd.n[0] * vd.n[1] : -(vd.n[0] * vd.n[1]);
   const unsigned int nvox = static_cast<unsigned int>(vd.n[0] * vd.n[1] * vd.n[2]);
   int lin = r.ient[0] + vd.n[0] * (r.ient[1] + vd.n[1] * r.ient[2]);
-  const float s = gL * r.unit;
+  constexpr int kShift = 27;
+  constexpr unsigned int kExit = kExitUnits << (32 - kShift);  // 2^29
+  const float s = gL * r.unit * (1.f / static_cast<float>(1u << (32 - kShift)));
   unsigned int ac = 0u;
   for (int m = 1; m < r.nseg; ++m) {
-    const unsigned int hx = hi32(Ax), hy = hi32(Ay), hz = hi32(Az);
+    const unsigned int hx = static_cast<unsigned int>(Ax >> kShift), hy = static_cast<unsigned int>(Ay >> kShift),
+                       hz = static_cast<unsigned int>(Az >> kShift);
     const unsigned int an = min(min(hx, hy), hz);
     if (static_cast<unsigned int>(lin) < nvox)
       atomicAdd(gvol + lin, s * static_cast<float>(static_cast<int>(an - ac)));
@@ -864,7 +886,7 @@ __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RayS
     if (bz) Az += r.D[2];
   }
   if (static_cast<unsigned int>(lin) < nvox)
-    atomicAdd(gvol + lin, s * static_cast<float>(static_cast<int>(kExitUnits - ac)));
+    atomicAdd(gvol + lin, s * static_cast<float>(static_cast<int>(kExit - ac)));
 }
 
 template <int MODE>
