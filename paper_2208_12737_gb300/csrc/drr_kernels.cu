@@ -454,9 +454,19 @@ constexpr int kFwdUnroll = DRR_FWD_UNROLL;
 constexpr int kJacUnroll = DRR_JAC_UNROLL;
 // Chunk length per ray.  The FP32 error of a local position grows with the
 // chunk's share of the ray, so long rays take long chunks (fewer exact
-// re-anchorings) and short rays short ones; 6k + 1 crossings (61, 31, 19, 13).
+// re-anchorings) and short rays short ones; 6k + 1 crossings.  The Jacobian
+// walk stays at 61 for long rays: its tie test's threshold grows with the
+// positions, so longer chunks are flagged (and walked twice) more often.  The
+// forward walk has no tie test and takes 121 / 181 for rays of more than 512 /
+// 1024 segments (on the CT workload: 3 % faster, worst pixel error unchanged).
+#ifndef DRR_JAC_LONG
+#define DRR_JAC_LONG 61
+#endif
 __device__ __forceinline__ int walk_chunk(int nseg) {
-  return nseg > 512 ? 61 : nseg > 256 ? 31 : nseg > 128 ? 19 : 13;
+  return nseg > 512 ? DRR_JAC_LONG : nseg > 256 ? 31 : nseg > 128 ? 19 : 13;
+}
+__device__ __forceinline__ int fwd_chunk(int nseg) {
+  return nseg > 1024 ? 181 : nseg > 512 ? 121 : walk_chunk(nseg);
 }
 
 // Forward walk (Eq. 2 with the crossings of Eq. 3 taken in order, Sec. 2.2).
@@ -479,7 +489,7 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
   float v = Voxel<DT>::load(vd.data, off);
   float acc = 0.f;
   int remaining = r.nseg - 1;
-  const int chunk = walk_chunk(r.nseg);
+  const int chunk = fwd_chunk(r.nseg);
   while (remaining > 0) {
     const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], kx), O);
     const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], ky), O);
