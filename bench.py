@@ -718,6 +718,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = seg * ops_per_seg / (k_ms * 1e-3) / 1e12
     peak_alu = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x max SM clock, tera-ops/s
     gather_gbs = seg * elem / (k_ms * 1e-3) / 1e9  # voxel gathers only
+    vol_bytes = int(np.prod(hu.shape)) * elem
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -735,7 +736,14 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak_alu, "traffic": profiled_traffic("siddon_fwd_jac"),
                      "kernel": "siddon_fwd_jac", "kernel_ms": k_ms,
                      "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({which} sm_max)",
-                     "gathered_gbs": gather_gbs},
+                     "gathered_gbs": gather_gbs,
+                     # the volume's compulsory first touch from HBM after the flush, per kernel launch
+                     "compulsory_hbm": {"bytes": vol_bytes, "achieved_gbs": vol_bytes / (k_ms * 1e-3) / 1e9,
+                                        "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+                                        "frac": vol_bytes / (k_ms * 1e-3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}},
+        "step_ms_stats": {"mean": statistics.mean(step_ms), "median": statistics.median(step_ms),
+                          "p99": float(np.quantile(step_ms, 0.99)), "min": min(step_ms), "max": max(step_ms),
+                          "rank": rank},
         "e2e": {"value": job_throughput(world, rays, ems), "unit": UNIT, "h2d_bytes_per_step": B * 6 * 4,
                 "d2h_bytes_per_step": B * H * W * 4 + B * 6 * 4},
         "graph_replay": ({"ms_per_step": graph_ms, "value": job_throughput(1, rays, graph_ms), "unit": UNIT}

@@ -66,6 +66,36 @@ def test_per_ray_jacobian_vs_oracle(drr):
         assert np.median(err) < 1e-6
 
 
+def test_jacobian_through_near_coincident_crossings(drr):
+    # cubic voxels seen at 45 degrees plus a few 1e-5 rad: pairs of x / y (and
+    # x / y / z) crossings lie closer than the FP32 walk resolves, so most
+    # chunks take the exact re-walk; the voxel between two near-coincident
+    # crossings, hence both crossings' weights, must follow the exact order
+    vol_np = inputs.ellipsoid_phantom((32, 32, 32), (1.0, 1.0, 1.0), seed=61)
+    vol = drr.Volume(vol_np, (1.0, 1.0, 1.0))
+    det = inputs.Detector(200.0, 24, 24, 1.0, 1.0)
+    q = np.pi / 4
+    c = np.arctan(1.0 / np.sqrt(2.0))  # with rz = 45 deg: the cube's body diagonal
+    poses_np = np.array([[q + 1e-5, 0, 0, 0.13, 0.07, 0.02], [q - 3e-5, 0, 0, -0.2, 0.1, 0.3],
+                         [0, q + 2e-5, 0, 0.05, -0.1, 0.2], [q + 1e-5, c + 2e-5, 0, 0.1, 0.05, -0.07]], np.float32)
+    P = torch.from_numpy(poses_np).cuda()
+    E, J = drr.render(vol, det, P, jacobian=True)
+    ov = ovol(vol_np, (1.0, 1.0, 1.0))
+    E_ref, J_ref = oracle.render(ov, odet(det), poses_np, jacobian=True)
+    assert rel_err(E.cpu().numpy(), E_ref).max() < FP32_TOL
+    J = J.cpu().numpy()
+    J_ref = np.moveaxis(J_ref, -1, 1)
+    for grp in (slice(0, 3), slice(3, 6)):
+        err = np.abs(J[:, grp] - J_ref[:, grp]) / np.abs(J_ref[:, grp]).max()
+        assert np.mean(err < 1e-4) > 0.999, np.sort(err.ravel())[-10:]
+    g_np = inputs.upstream_grad((4, 24, 24), seed=62)
+    G_ref = oracle.pose_grad(ov, odet(det), poses_np, g_np.astype(np.float64))
+    g = torch.from_numpy(g_np).cuda()
+    for G in (drr.render_backward(vol, det, P, g, jac=J_t) for J_t in (torch.from_numpy(np.ascontiguousarray(J)).cuda(), None)):
+        G = G.cpu().numpy()
+        assert grad_err(G, G_ref).max() < GRAD_TOL, grad_err(G, G_ref)
+
+
 def test_ct_full_size_pose_gradient(drr):
     # the benchmarked workload: 512x512x133, 200x200, 16 poses; oracle on 2 poses
     cfg = inputs.CT
