@@ -676,12 +676,21 @@ def run_ours(args, rank, world, local_rank):
     G_h = torch.empty((B, 6), dtype=torch.float32).pin_memory()
     poses_d = torch.empty_like(poses)
 
+    copy_stream = torch.cuda.Stream()
+    e_ready = torch.cuda.Event()
+
     def e2e():
+        # the DRR goes back to the host on a side stream while the gradient reduction runs
+        main = torch.cuda.current_stream()
         poses_d.copy_(poses_h, non_blocking=True)
         drr.render(vol, det, poses_d, jacobian=True, out=E, jac=J)
+        e_ready.record(main)
+        copy_stream.wait_event(e_ready)
+        with torch.cuda.stream(copy_stream):
+            E_h.copy_(E, non_blocking=True)
         G = drr.render_backward(vol, det, poses_d, g, jac=J)
-        E_h.copy_(E, non_blocking=True)
         G_h.copy_(G, non_blocking=True)
+        main.wait_stream(copy_stream)
 
     e2e_ms = timed(e2e, args.steps)
     # the same step captured once in a CUDA graph and replayed (no host launch work per step)

@@ -435,6 +435,24 @@ __device__ __forceinline__ float fix_to_float(long long d) {
   return fmaf(static_cast<float>(static_cast<unsigned int>(d)), kTwoM32, static_cast<float>(static_cast<int>(d >> 32)));
 }
 
+// Next crossings of two axes, l * delta + x0 each, in one packed two-lane FP32
+// FMA (each lane rounded as fmaf rounds it, so the results are the same);
+// -DDRR_PACKED_XY=0 issues two scalar FMAs.
+#ifndef DRR_PACKED_XY
+#define DRR_PACKED_XY 1
+#endif
+__device__ __forceinline__ void next_xy(float& tx, float& ty, float lx, float ly, float dx, float dy, float x0,
+                                        float y0) {
+#if DRR_PACKED_XY
+  const float2 t = __ffma2_rn(make_float2(lx, ly), make_float2(dx, dy), make_float2(x0, y0));
+  tx = t.x;
+  ty = t.y;
+#else
+  tx = fmaf(lx, dx, x0);
+  ty = fmaf(ly, dy, y0);
+#endif
+}
+
 // Local FP32 position of an exact position relative to O.
 __device__ __forceinline__ float local_pos(unsigned long long x, unsigned long long O) {
   return fix_to_float(static_cast<long long>(x - O));
@@ -507,8 +525,7 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
     if (bx) lx += 1.f;                                      \
     if (by) ly += 1.f;                                      \
     if (bz) lz += 1.f;                                      \
-    tx = fmaf(lx, dx, x0);                                  \
-    ty = fmaf(ly, dy, y0);                                  \
+    next_xy(tx, ty, lx, ly, dx, dy, x0, y0);                \
     tz = fmaf(lz, dz, z0);                                  \
   }
     DRR_FSTEP(a1)
@@ -628,8 +645,7 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     if (bx) lx += 1.f;                                     \
     if (by) ly += 1.f;                                     \
     if (bz) lz += 1.f;                                     \
-    tx = fmaf(lx, dl[0], x0);                              \
-    ty = fmaf(ly, dl[1], y0);                              \
+    next_xy(tx, ty, lx, ly, dl[0], dl[1], x0, y0);         \
     tz = fmaf(lz, dl[2], z0);                              \
   }
 #define DRR_JAC_ACCOUNT()                                  \
