@@ -124,18 +124,32 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def profiled_traffic(kernel="siddon_fwd_jac"):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def profiled_value(key, kernel="siddon_fwd_jac"):
+    """A per-launch figure (`key: N source_sha256: H`) from the committed ncu summary
+    of `kernel`, if it was taken on the current kernel source; else None."""
     import glob
     import re
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}__*.md"))):
         with open(path) as f:
             text = f.read()
-        m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source_sha256:\s*([0-9a-f]{64})", text)
+        m = re.search(key + r":\s*(\d+)\s+source_sha256:\s*([0-9a-f]{64})", text)
         if m and m.group(2) == kernel_source_hash():
             return int(m.group(1))
     return None
+
+
+def profiled_traffic(kernel="siddon_fwd_jac"):
+    """DRAM bytes per launch of `kernel` (ncu), for the current kernel source; else None."""
+    return profiled_value("traffic_bytes_per_launch", kernel)
+
+
+def issue_roofline(kernel_ms, sm_max_mhz):
+    inst = profiled_value("warp_instructions_per_launch")
+    peak = 4 * 152 * sm_max_mhz * 1e6 / 1e9  # G warp-instructions/s
+    if inst is None:
+        return {"achieved_ginst_s": None, "peak_ginst_s": peak, "frac": None}
+    ach = inst / (kernel_ms * 1e-3) / 1e9
+    return {"achieved_ginst_s": ach, "peak_ginst_s": peak, "frac": ach / peak, "inst_per_launch": inst}
 
 
 def workload_inputs(rank=0):
@@ -746,6 +760,9 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": "siddon_fwd_jac", "kernel_ms": k_ms,
                      "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({which} sm_max)",
                      "gathered_gbs": gather_gbs,
+                     # issued warp instructions (ncu count per launch, current source only) per
+                     # second of the event-timed launch, against 4 schedulers x SMs x max clock
+                     "issue": issue_roofline(k_ms, sm_max),
                      # the volume's compulsory first touch from HBM after the flush, per kernel launch
                      "compulsory_hbm": {"bytes": vol_bytes, "achieved_gbs": vol_bytes / (k_ms * 1e-3) / 1e9,
                                         "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
