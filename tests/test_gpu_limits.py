@@ -81,6 +81,26 @@ def test_long_rays(drr):
     assert n.max() == oracle.count_segments((3, 5, 3000), osp(sp), odet(det), poses_np).max() > 3000
 
 
+def test_geometry_just_inside_the_length_limit(drr):
+    # longest ray / smallest voxel = 0.95 * 2^20: micrometre voxels seen from ~1 m
+    rng = np.random.default_rng(88)
+    vol_np = rng.uniform(0.0, 50.0, (4, 5, 6)).astype(np.float32)
+    sp = (1e-3, 1.2e-3, 1.1e-3)
+    vol = drr.Volume(vol_np, sp)
+    det = inputs.Detector(999.0, 6, 7, 1.5e-3, 1.4e-3)
+    poses_np = np.array([[0, 0, 0, 0, 0, 0], [0.3, -0.2, 0.1, 1e-4, -2e-4, 1e-4], [1.2, 0.4, -0.7, 0, 0, 0]],
+                        np.float32)
+    P = torch.from_numpy(poses_np).cuda()
+    E, J = drr.render(vol, det, P, jacobian=True)
+    E_ref = oracle.render(ovol(vol_np, sp), odet(det), poses_np)
+    assert (E_ref > 0).mean() > 0.5
+    assert rel_err(E.cpu().numpy(), E_ref).max() < FP32_TOL
+    g_np = inputs.upstream_grad((3, 6, 7), seed=89)
+    G = drr.render_backward(vol, det, P, torch.from_numpy(g_np).cuda(), jac=J).cpu().numpy()
+    G_ref = oracle.pose_grad(ovol(vol_np, sp), odet(det), poses_np, g_np.astype(np.float64))
+    assert grad_err(G, G_ref).max() < GRAD_TOL, grad_err(G, G_ref)
+
+
 def test_size_limits_are_rejected(drr):
     vol = drr.Volume(np.ones((4, 4, 4), np.float32), (1.0, 1.0, 1.0))
     P = torch.zeros((1, 6), device="cuda")
