@@ -41,7 +41,8 @@ struct PoseGeom {
   float u0f[3];   // FP32 copies of u0, un for the coarse clip
   float unf[3];
   // Chain-rule terms for the pose Jacobian, world units (mm), j = angle index:
-  float S[3][3];   // dR/d eta_j * s_c
+  float Om[3][3];  // omega_j: dR/d eta_j R^T x = omega_j x x (the angle's angular velocity)
+  float t[3];      // the pose translation
   float Q[3][3];   // dR/d eta_j * (p_c(0,0) - s_c)
   float Wv[3][3];  // dR/d eta_j * (0, dw, 0)
   float Hv[3][3];  // dR/d eta_j * (0, 0, dh)

@@ -125,7 +125,8 @@ __device__ void apply3f(const float* A, const float* x, float* y) {
 
 // FP32 chain-rule terms of one pose (dR/d eta_j applied to s_c, p_c - s_c and the
 // pixel steps), from the FP32-rounded sines and cosines: they are stored as FP32.
-__device__ void chain_terms(const float cs[6], double rho, double pw, double ph, const DetDev& det, PoseGeom* g) {
+__device__ void chain_terms(const float cs[6], const float t[3], double rho, double pw, double ph, const DetDev& det,
+                            PoseGeom* g) {
   const float sz = cs[0], cz = cs[1], sy = cs[2], cy = cs[3], sx = cs[4], cx = cs[5];
   const float Rz[9] = {cz, -sz, 0.f, sz, cz, 0.f, 0.f, 0.f, 1.f};
   const float Ry[9] = {cy, 0.f, sy, 0.f, 1.f, 0.f, -sy, 0.f, cy};
@@ -140,17 +141,22 @@ __device__ void chain_terms(const float cs[6], double rho, double pw, double ph,
   mul3f(Rz, dRy, U);
   mul3f(U, Rx, dR + 9);
   mul3f(T, dRx, dR + 18);
-  const float scf[3] = {static_cast<float>(rho), 0.f, 0.f};
+  // angular velocities of the three angles in the world frame, dR_j R^T x =
+  // omega_j x x: rz turns about e_z, ry about Rz e_y, rx about Rz Ry e_x
+  const float om[9] = {0.f, 0.f, 1.f, -sz, cz, 0.f, cz * cy, sz * cy, -sy};
   const float q[3] = {static_cast<float>(-2.0 * rho), static_cast<float>(pw), static_cast<float>(ph)};
   const float vw[3] = {0.f, det.dw, 0.f};
   const float vh[3] = {0.f, 0.f, det.dh};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    apply3f(dR + 9 * j, scf, g->S[j]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g->Om[j][a] = om[3 * j + a];
     apply3f(dR + 9 * j, q, g->Q[j]);
     apply3f(dR + 9 * j, vw, g->Wv[j]);
     apply3f(dR + 9 * j, vh, g->Hv[j]);
   }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g->t[a] = t[a];
   g->hc = 0.5f * static_cast<float>(det.H - 1);
   g->wc = 0.5f * static_cast<float>(det.W - 1);
 }
@@ -203,7 +209,8 @@ __device__ void warp_pose_geom(const float* pose, const DetDev& det, const Volum
   if (lane == 0) {
     const float cs[6] = {static_cast<float>(sz), static_cast<float>(cz), static_cast<float>(sy),
                          static_cast<float>(cy), static_cast<float>(sx), static_cast<float>(cx)};
-    chain_terms(cs, rho, pw, ph, det, g);
+    const float tr[3] = {pose[3], pose[4], pose[5]};
+    chain_terms(cs, tr, rho, pw, ph, det, g);
   }
 }
 
@@ -297,12 +304,15 @@ __device__ __forceinline__ int floor_fast(double x) {
 }
 
 // FP64 clip (Sec. 2.3, clamped to [0, 1]), entry/exit voxels and first
-// crossings.  The faces the ray enters and leaves through are found in FP32;
-// alpha_min / alpha_max are then evaluated in FP64 on those faces.  (Where two
-// faces tie to FP32 precision -- a ray through a box edge -- either choice
-// changes the entry by less than 1e-7 of alpha.)  Returns 1 for a hit, 0 when
-// the ray misses, -1 for non-finite geometry.
-__device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg, int h, int w, RaySetup& r) {
+// crossings.  The faces the ray enters and leaves through are found in FP32
+// (in FP64 where FP32 cannot tell them apart); alpha_min / alpha_max are then
+// evaluated in FP64 on those faces.  Returns 1 for a hit, 0 when the ray
+// misses, -1 for non-finite geometry.
+// kEntry: also the entry point s + amin (p - s) in world coordinates (mm, from
+// the FP64 entry) into e[3], for the pose Jacobian.
+template <bool kEntry>
+__device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg, int h, int w, RaySetup& r,
+                                         float* e = nullptr) {
   double g[3];
   float gf[3];
   bool finite = true;
@@ -314,7 +324,13 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
   }
   r.nseg = 0;
   if (!finite) return -1;
-  float lof = 0.f, hif = 1.f;
+  // faces in FP32; a choice that FP32 cannot make safely -- the runner-up
+  // crossing (or the clamp at alpha 0 / 1) within 2^-20 of the chosen one, four
+  // times the FP32 error of these products, or a hit test that close -- is
+  // made again in FP64.  That matters where the clipped span is a small part of
+  // alpha (a small volume far from the source): there an FP32 tie moves the
+  // entry by a visible share of the span.
+  float lof = 0.f, hif = 1.f, lo2 = -1.f, hi2 = 2.f;  // chosen and runner-up entry / exit
   int ea = -1, xa = -1;
   bool hit = true;
 #pragma unroll
@@ -323,22 +339,38 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
       const float rf = __frcp_rn(gf[a]);
       const float t0 = -pg.u0f[a] * rf, t1 = pg.unf[a] * rf;
       const float lo = fminf(t0, t1), hi = fmaxf(t0, t1);
-      if (lo > lof) { lof = lo; ea = a; }
-      if (hi < hif) { hif = hi; xa = a; }
+      if (lo > lof) { lo2 = lof; lof = lo; ea = a; } else lo2 = fmaxf(lo2, lo);
+      if (hi < hif) { hi2 = hif; hif = hi; xa = a; } else hi2 = fminf(hi2, hi);
     } else if (!(pg.u0[a] >= 0.0 && pg.un[a] > 0.0)) {
       hit = false;
     }
   }
-  if (!hit || !(lof < hif)) return 0;
+  if (!hit) return 0;
+  const float tol = 9.5367431640625e-7f * fmaxf(fabsf(lof), fabsf(hif)) + 1e-30f;  // 2^-20
+  const bool exact = lof - lo2 < tol || hi2 - hif < tol || fabsf(hif - lof) < tol;
+  if (!exact && !(lof < hif)) return 0;
   double rg[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) rg[a] = g[a] != 0.0 ? rcp_fast(g[a]) : 0.0;
   // entry / exit faces: plane 0 when the ray runs up the axis, plane n otherwise
   double amin = 0.0, amax = 1.0;
+  if (exact) {
+    ea = xa = -1;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {  // static indices: the arrays stay in registers
-    if (a == ea) amin = (g[a] > 0.0 ? -pg.u0[a] : pg.un[a]) * rg[a];
-    if (a == xa) amax = (g[a] > 0.0 ? pg.un[a] : -pg.u0[a]) * rg[a];
+    for (int a = 0; a < 3; ++a) {
+      if (g[a] != 0.0) {
+        const double en = (g[a] > 0.0 ? -pg.u0[a] : pg.un[a]) * rg[a];
+        const double ex = (g[a] > 0.0 ? pg.un[a] : -pg.u0[a]) * rg[a];
+        if (en > amin) { amin = en; ea = a; }
+        if (ex < amax) { amax = ex; xa = a; }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {  // static indices: the arrays stay in registers
+      if (a == ea) amin = (g[a] > 0.0 ? -pg.u0[a] : pg.un[a]) * rg[a];
+      if (a == xa) amax = (g[a] > 0.0 ? pg.un[a] : -pg.u0[a]) * rg[a];
+    }
   }
   if (!(amin < amax)) return 0;
   r.ea = ea;
@@ -352,6 +384,10 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
   for (int a = 0; a < 3; ++a) {
     const int n = vd.n[a];
     r.d[a] = gf[a] * vd.delta[a];
+    // entry position u_e (voxel units) and its world point (volume centred at
+    // the origin); u_e lies in [0, n], so FP32 holds it to ~1e-7 voxel
+    const double ue = fma(amin, g[a], pg.u0[a]);
+    if (kEntry) e[a] = fmaf(static_cast<float>(ue), vd.delta[a], -0.5f * static_cast<float>(n) * vd.delta[a]);
     if (g[a] == 0.0) {
       r.ient[a] = min(max(static_cast<int>(floor(pg.u0[a])), 0), n - 1);
       r.cnt[a] = 0;
@@ -361,7 +397,6 @@ __device__ __forceinline__ int ray_setup(const VolumeDev& vd, const PoseGeom& pg
       continue;
     }
     const bool up = g[a] > 0.0;
-    const double ue = fma(amin, g[a], pg.u0[a]);
     const double ux = fma(amax, g[a], pg.u0[a]);
     int i0, i1;
     if (a == ea) i0 = up ? 0 : n - 1;
@@ -417,6 +452,7 @@ struct WalkScratch {
 // declares only what its walk uses.)
 struct JacScratch : WalkScratch {
   int cnt[3][kThreads];  // crossings per slot (read only by the exact re-walk)
+  float e[3][kThreads];  // the ray's entry point (read only by the Jacobian epilogue)
   int c_off[kThreads];
   float c_v[kThreads], c_vprev[kThreads];
   int c_pend[kThreads];
@@ -852,15 +888,14 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
 // which has no cancellation for rays nearly along that axis.
 //   dE/d eta_j = dE/dt . (dR_j s_c) + dE/dp . (dR_j (p_c - s_c)).
 // gt = dE/dt, gp = dE/dp in world units.
-__device__ __forceinline__ void ray_world_grads(const RaySetup& r, const JacSums& s, float gt[3], float gp[3]) {
+__device__ __forceinline__ void ray_world_grads(const RaySetup& r, const JacSums& s, float gt[3], float q[3]) {
   const float L2 = fmaf(r.d[2], r.d[2], fmaf(r.d[1], r.d[1], r.d[0] * r.d[0]));
   const float L = sqrtf(L2);
   const float F = s.F;
-  const float am = static_cast<float>(r.amin);
-  float R = fmaf(am, s.Gc, s.Ac);
+  float R = s.Ac;  // position sums relative to the entry
 #pragma unroll
   for (int a = 0; a < 3; ++a)
-    if (a != s.dom) R += fmaf(am, s.G[a], s.A[a]);
+    if (a != s.dom) R += s.A[a];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (r.d[a] != 0.f) {
@@ -871,31 +906,31 @@ __device__ __forceinline__ void ray_world_grads(const RaySetup& r, const JacSums
 #pragma unroll
         for (int b = 0; b < 3; ++b)
           if (b != a) D = fmaf(r.d[b], r.d[b], D);
-        gp[a] = (L * R - F * D / L) / r.d[a];
+        q[a] = (L * R - F * D / L) / r.d[a];
       } else {
-        gp[a] = r.d[a] * F / L - fmaf(am, s.G[a], s.A[a]) * Ld;
+        q[a] = r.d[a] * F / L - s.A[a] * Ld;
       }
     } else {
       gt[a] = 0.f;
-      gp[a] = 0.f;
+      q[a] = 0.f;
     }
   }
 }
 
-__device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& s, const PoseGeom& pg, int h, int w,
-                                              float scale, float J[6]) {
-  float gt[3], gp[3];
-  ray_world_grads(r, s, gt, gp);
+__device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& s, const PoseGeom& pg,
+                                              const float e[3], int h, int w, float scale, float J[6]) {
+  float gt[3], q[3];
+  ray_world_grads(r, s, gt, q);
+  // an angle moves the entry point e by omega_j x (e - t): its term is
+  // gt . (omega_j x (e - t)) = omega_j . ((e - t) x gt)
+  const float x0 = e[0] - pg.t[0], x1 = e[1] - pg.t[1], x2 = e[2] - pg.t[2];
+  const float c0 = fmaf(x1, gt[2], -x2 * gt[1]), c1 = fmaf(x2, gt[0], -x0 * gt[2]), c2 = fmaf(x0, gt[1], -x1 * gt[0]);
   const float fw = static_cast<float>(w), fh = static_cast<float>(h);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    float acc = 0.f;
+    float acc = fmaf(pg.Om[j][0], c0, fmaf(pg.Om[j][1], c1, pg.Om[j][2] * c2));
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float Dja = fmaf(fh, pg.Hv[j][a], fmaf(fw, pg.Wv[j][a], pg.Q[j][a]));
-      acc = fmaf(gt[a], pg.S[j][a], acc);
-      acc = fmaf(gp[a], Dja, acc);
-    }
+    for (int a = 0; a < 3; ++a) acc = fmaf(q[a], fmaf(fh, pg.Hv[j][a], fmaf(fw, pg.Wv[j][a], pg.Q[j][a])), acc);
     J[j] = acc * scale;
   }
 #pragma unroll
@@ -910,14 +945,17 @@ __device__ __forceinline__ void pose_jacobian(const RaySetup& r, const JacSums& 
 //   dE/ddh  = (h - hc) dE/dp . R e_z,   dE/ddw = (w - wc) dE/dp . R e_y.
 __device__ __forceinline__ void geometry_jacobian(const RaySetup& r, const JacSums& s, const PoseGeom& pg, int h,
                                                   int w, float scale, float J[3]) {
-  float gt[3], gp[3];
-  ray_world_grads(r, s, gt, gp);
+  float gt[3], q[3];
+  ray_world_grads(r, s, gt, q);
+  // dE/dp = q + amin gt; dE/ds - dE/dp = gt - 2 dE/dp = (1 - 2 amin) gt - 2 q
+  const float am = static_cast<float>(r.amin), c = static_cast<float>(1.0 - 2.0 * r.amin);
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    a0 = fmaf(gt[a] - 2.f * gp[a], pg.Rc[0][a], a0);
-    a1 = fmaf(gp[a], pg.Rc[2][a], a1);
-    a2 = fmaf(gp[a], pg.Rc[1][a], a2);
+    const float gp = fmaf(am, gt[a], q[a]);
+    a0 = fmaf(fmaf(c, gt[a], -2.f * q[a]), pg.Rc[0][a], a0);
+    a1 = fmaf(gp, pg.Rc[2][a], a1);
+    a2 = fmaf(gp, pg.Rc[1][a], a2);
   }
   J[0] = 0.5f * a0 * scale;
   J[1] = (static_cast<float>(h) - pg.hc) * a1 * scale;
@@ -983,8 +1021,15 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
   res.nseg = 0;
 #pragma unroll
   for (int k = 0; k < 6; ++k) res.J[k] = 0.f;
+  constexpr bool kJac = MODE == kFwdJac || MODE == kPoseGrad || MODE == kGeoGrad;
   RaySetup r;
-  const int rs = ray_setup(vd, pg, h, w, r);
+  float e[3];
+  const int rs = ray_setup<kJac>(vd, pg, h, w, r, e);
+  if (kJac && rs > 0) {  // parked in shared memory until the epilogue
+    JacScratch* js = static_cast<JacScratch*>(ws);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) js->e[a][threadIdx.x] = e[a];
+  }
   if (rs < 0) {  // non-finite geometry (e.g. a NaN pose): NaN out, no walk
     res.F = __int_as_float(0x7fffffff);
 #pragma unroll
@@ -1005,7 +1050,9 @@ __device__ __forceinline__ void trace_ray(const VolumeDev& vd, const PoseGeom& p
       geometry_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
       res.J[3] = res.J[4] = res.J[5] = 0.f;
     } else {
-      pose_jacobian(r, s, pg, h, w, vd.out_scale, res.J);
+      const JacScratch* js = static_cast<const JacScratch*>(ws);
+      const float ep[3] = {js->e[0][threadIdx.x], js->e[1][threadIdx.x], js->e[2][threadIdx.x]};
+      pose_jacobian(r, s, pg, ep, h, w, vd.out_scale, res.J);
     }
   } else if (MODE == kBackproject) {
     walk_backproject(vd, r, gscale * L, gvol);
