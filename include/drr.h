@@ -26,6 +26,11 @@
  *    message (thread-local, valid until the next failing call on that thread).
  *  - Empty work (B == 0, H*W == 0) and non-positive sizes or spacings are
  *    DRR_ERR_INVALID.  Non-finite poses give NaN outputs, not an error.
+ *  - Limits, checked on the host before any device work (DRR_ERR_INVALID):
+ *    B <= 65535 poses per call; H*W <= 2^30 pixels; B * ceil(W/8) * ceil(H/4)
+ *    < 2^31; (nx+2)(ny+2)(nz+2) < 2^31 voxels; longest ray |p - s| divided by
+ *    the smallest voxel spacing < 2^20 (the walk's FP32 positions need the
+ *    plane spacing well above their resolution).
  */
 #ifndef DRR_H_
 #define DRR_H_
@@ -74,10 +79,11 @@ typedef struct {
   drr_dtype storage;  /* DRR_F32 (default), DRR_BF16 or DRR_F16 */
   float hu_mu_water;  /* attenuation of water in /mm for DRR_I16_HU input:
                          mu = max(0, mu_water (1 + HU/1000)); 0 -> 0.02 */
-  int32_t layout;     /* 0 = default; 1 = padded linear (x fastest);
-                         2 = bricked (brick edges below) */
-  int32_t brick[3];   /* brick edge in voxels along x, y, z (powers of two, <= 64);
-                         used when layout == 2 */
+  int32_t layout;     /* 0 = default = 1 = padded linear (x fastest, one zero
+                         voxel of padding per face): the only layout; other
+                         values are DRR_ERR_INVALID (a bricked layout adds
+                         per-step work to a walk bound by instruction issue) */
+  int32_t brick[3];   /* reserved, ignored */
 } drr_volume_options;
 
 /* ---- volumes (Sec. 2.2: the CT volume V and its spacing) ---------------- */
