@@ -600,9 +600,10 @@ def adjoint_bench(drr, vol, det, poses, g, hu_shape, rays, reps=3):
             "what": "dL/dV by back-projection (exact fixed-point re-walk, FP32 atomics) for the 16-pose batch"}
 
 
-def fd_baseline(drr, vol, det, poses, rays, reps=3):
+def fd_baseline(drr, vol, det, poses, rays, reps=3, plain=False):
     """The finite-difference alternative to the analytic pose gradient: central differences
-    need 12 extra forward renders per pose (13 with the DRR itself), timed as one batch."""
+    need 12 extra forward renders per pose (13 with the DRR itself), timed as one batch;
+    with plain=True on the plain FP32 forward walk instead of the exact one."""
     import torch
     P = poses.repeat(13, 1).contiguous()
     steps = torch.tensor([1e-3] * 3 + [1e-2] * 3, device=poses.device)
@@ -610,19 +611,22 @@ def fd_baseline(drr, vol, det, poses, rays, reps=3):
         P[(1 + 2 * k) * len(poses):(2 + 2 * k) * len(poses), k] += steps[k]
         P[(2 + 2 * k) * len(poses):(3 + 2 * k) * len(poses), k] -= steps[k]
     out = torch.empty((P.shape[0], det.height, det.width), device=poses.device)
-    drr.render(vol, det, P, out=out)
+    render = drr.render_plain_fp32 if plain else drr.render
+    render(vol, det, P, out=out)
     torch.cuda.synchronize()
     ms = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        drr.render(vol, det, P, out=out)
+        render(vol, det, P, out=out)
         b.record()
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     t = statistics.median(ms)
+    walk = "the plain FP32 forward walk" if plain else "the exact forward walk"
     return {"ms_per_step": t, "value": rays / (t * 1e-3) / 1e9, "unit": UNIT,
-            "what": "DRR + central-difference pose gradient: 13 forward renders per pose (h = 1e-3 rad, 1e-2 mm)"}
+            "what": f"DRR + central-difference pose gradient: 13 renders per pose by {walk} "
+                    "(h = 1e-3 rad, 1e-2 mm)"}
 
 
 def registration_bench(drr, hu, lr_rot=1e-2, lr_trans=1.0):
@@ -866,6 +870,7 @@ def run_ours(args, rank, world, local_rank):
         line["roofline"]["gather"] = {"achieved_gbs": gather_gbs, "peak_gbs": l2, "frac": gather_gbs / l2,
                                       "peak_source": "measured: 64 MB L2-resident buffer streamed with 16-byte loads"}
         line["fd_baseline"] = fd_baseline(drr, vol, det, poses, rays)
+        line["fd_baseline_plain_fp32"] = fd_baseline(drr, vol, det, poses, rays, plain=True)
         line["volume_adjoint"] = adjoint_bench(drr, vol, det, poses, g, hu.shape, rays)
         drr.render(vol, det, poses, out=E)
         line["plain_fp32_baseline"] = plain_fp32_baseline(drr, vol, det, poses, E, rays)
