@@ -28,7 +28,8 @@
  *    DRR_ERR_INVALID.  Non-finite poses give NaN outputs, not an error.
  *  - Limits, checked on the host before any device work (DRR_ERR_INVALID):
  *    B <= 65535 poses per call; H*W <= 2^30 pixels; B * ceil(W/8) * ceil(H/4)
- *    < 2^31; (nx+2)(ny+2)(nz+2) < 2^31 voxels; longest ray |p - s| divided by
+ *    and B * ceil(W/4) * ceil(H/8) < 2^31 (warp tiles of the walks and of the
+ *    back-projection); (nx+2)(ny+2)(nz+2) < 2^31 voxels; longest ray |p - s| divided by
  *    the smallest voxel spacing < 2^20 (the walk's FP32 positions need the
  *    plane spacing well above their resolution).
  */

@@ -184,7 +184,8 @@ drr_status setup_geometry(drr_volume v, const drr::DetDev& dd, const float* pose
                           AsyncBuf<drr::PoseGeom>& pg) {
   // one PoseGeom per pose plus one slot for the walk kernels' tile counters
   static_assert(sizeof(drr::PoseGeom) >= drr::kLaunchCounters * sizeof(unsigned int), "counter slot");
-  if (int64_t(drr::pose_tiles(dd)) * B >= (int64_t{1} << 31))
+  if (int64_t(drr::pose_tiles(dd) > drr::bp_pose_tiles(dd) ? drr::pose_tiles(dd) : drr::bp_pose_tiles(dd)) * B >=
+      (int64_t{1} << 31))
     return drr::set_error(DRR_ERR_INVALID, "too many rays in one call (B * pixels / 32 must stay below 2^31)");
   DRR_CUDA(pg.alloc(size_t(B) + 1, st), "cudaMallocAsync(pose geometry)");
   LaunchScope ls(kPoseSetup, st);

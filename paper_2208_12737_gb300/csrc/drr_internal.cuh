@@ -22,6 +22,14 @@ constexpr int kThreads = 256;
 constexpr int kWarpTileW = DRR_WARP_TILE_W;
 constexpr int kWarpTileH = 32 / kWarpTileW;
 static_assert(kWarpTileW >= 4 && kWarpTileW <= 32 && 32 % kWarpTileW == 0, "warp tile width");
+// The back-projection walks 4 x 8 pixel tiles instead: its atomic adds are
+// merged down the tile's columns, and longer columns merge more (rays a pixel
+// apart along h often cross the same voxel).
+#ifndef DRR_BP_TILE_W
+#define DRR_BP_TILE_W 4
+#endif
+constexpr int kBpTileW = DRR_BP_TILE_W;
+static_assert(kBpTileW >= 1 && kBpTileW <= 32 && 32 % kBpTileW == 0, "back-projection tile width");
 
 // Tile counters of the walk kernels, kept in the geometry buffer right after the
 // last pose's PoseGeom and zeroed by the pose-setup kernel.
@@ -72,6 +80,11 @@ struct DetDev {
 // Warp tiles (kWarpTileW x kWarpTileH pixels) per pose: the work units of the walk kernels.
 __host__ __device__ __forceinline__ int pose_tiles(const DetDev& det) {
   return ((det.W + kWarpTileW - 1) / kWarpTileW) * ((det.H + kWarpTileH - 1) / kWarpTileH);
+}
+
+// Warp tiles per pose of the back-projection.
+__host__ __device__ __forceinline__ int bp_pose_tiles(const DetDev& det) {
+  return ((det.W + kBpTileW - 1) / kBpTileW) * ((det.H + 32 / kBpTileW - 1) / (32 / kBpTileW));
 }
 
 // One admitted request as the serving kernels see it (device-resident table).
