@@ -84,6 +84,10 @@ def _load():
                                            ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32,
                                            _dp, _dp]
         lib.oracle_backproject.restype = ctypes.c_int
+        lib.oracle_voxel_adjoint.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32, _dp,
+                                             _i64p, ctypes.c_int64, _dp, _dp]
+        lib.oracle_voxel_adjoint.restype = ctypes.c_int
         lib.oracle_count_segments.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32, _i64p,
                                               ctypes.c_int64, _ip]
@@ -255,6 +259,31 @@ def backproject(shape_zyx, spacing, det, poses, grad_out):
                            float(dh), float(dw), _ptr(poses, ctypes.c_float), int(B), _ptr(g, ctypes.c_double),
                            _ptr(out, ctypes.c_double))
     return out
+
+
+def voxel_adjoint(shape_zyx, spacing, det, poses, grad_out, voxels):
+    """The transpose of V -> E at the voxels with linear indices `voxels`
+    (i + nx (j + ny k)), by its definition: the sum over every ray of
+    g |p - s| times the ray's clipped chord (in alpha) through the voxel's box,
+    slab method per voxel as in the brute force of Eq. (1).  Returns the values
+    and the same sums with |g| (their rounding-error scale)."""
+    lib = _load()
+    sdr, H, W, dh, dw = det
+    nz, ny, nx = shape_zyx
+    n = np.array([nx, ny, nz], dtype=np.int32)
+    delta = np.array(spacing, dtype=np.float64)
+    poses = _c(poses, np.float32).reshape(-1, 6)
+    B = poses.shape[0]
+    g = _c(grad_out, np.float64).reshape(B, H, W)
+    vox = _c(voxels, np.int64).reshape(-1)
+    out = np.zeros(vox.size)
+    out_abs = np.zeros(vox.size)
+    if lib.oracle_voxel_adjoint(_ptr(n, ctypes.c_int32), _ptr(delta, ctypes.c_double), float(sdr), int(H), int(W),
+                                float(dh), float(dw), _ptr(poses, ctypes.c_float), int(B), _ptr(g, ctypes.c_double),
+                                _ptr(vox, ctypes.c_int64), int(vox.size), _ptr(out, ctypes.c_double),
+                                _ptr(out_abs, ctypes.c_double)) != 0:
+        raise MemoryError("oracle_voxel_adjoint: allocation failed")
+    return out, out_abs
 
 
 def count_segments(shape_zyx, spacing, det, poses, pixels=None):

@@ -489,6 +489,81 @@ int oracle_backproject(const int32_t n[3], const double delta[3], double sdr, in
   return 0;
 }
 
+/* The transpose of V -> E at selected voxels, straight from its definition
+ * (Eq. 1 with a piecewise-constant volume is linear in V): the adjoint at voxel
+ * v is the sum over all rays of g * |p - s| * (the length, in alpha, of the
+ * segment s->p clipped to v's box), the clip by the slab method as in
+ * oracle_brute_ray.  Also returns, per voxel, the same sum with |g|: the scale
+ * of the rounding error of any sum of these terms.  vox holds linear indices
+ * i + nx (j + ny k).  OpenMP over the selected voxels. */
+int oracle_voxel_adjoint(const int32_t n[3], const double delta[3], double sdr, int32_t H, int32_t W,
+                         double dh, double dw, const float* poses, int32_t B, const double* grad_out,
+                         const int64_t* vox, int64_t nsel, double* out, double* out_abs) {
+  const int64_t nray = (int64_t)B * H * W;
+  double* S = (double*)malloc(sizeof(double) * 3 * (size_t)nray);
+  double* Dv = (double*)malloc(sizeof(double) * 3 * (size_t)nray);
+  double* L = (double*)malloc(sizeof(double) * (size_t)nray);
+  if (!S || !Dv || !L) {
+    free(S);
+    free(Dv);
+    free(L);
+    return -1;
+  }
+  for (int32_t bi = 0; bi < B; ++bi) {
+    double pose[6];
+    for (int k = 0; k < 6; ++k) pose[k] = (double)poses[6 * bi + k];
+    for (int32_t h = 0; h < H; ++h)
+      for (int32_t w = 0; w < W; ++w) {
+        const int64_t r = ((int64_t)bi * H + h) * W + w;
+        double s[3], p[3];
+        oracle_ray_endpoints(pose, sdr, H, W, dh, dw, h, w, s, p);
+        for (int a = 0; a < 3; ++a) {
+          S[3 * r + a] = s[a];
+          Dv[3 * r + a] = p[a] - s[a];
+        }
+        L[r] = sqrt(Dv[3 * r] * Dv[3 * r] + Dv[3 * r + 1] * Dv[3 * r + 1] + Dv[3 * r + 2] * Dv[3 * r + 2]);
+      }
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t q = 0; q < nsel; ++q) {
+    const int64_t v = vox[q];
+    const int64_t id[3] = {v % n[0], (v / n[0]) % n[1], v / ((int64_t)n[0] * n[1])};
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+      const double b = -0.5 * (double)n[a] * delta[a];
+      lo[a] = b + (double)id[a] * delta[a];
+      hi[a] = b + (double)(id[a] + 1) * delta[a];
+    }
+    double acc = 0.0, acc_abs = 0.0;
+    for (int64_t r = 0; r < nray; ++r) {
+      const double* s = S + 3 * r;
+      const double* d = Dv + 3 * r;
+      double t_lo = 0.0, t_hi = 1.0;
+      int empty = 0;
+      for (int a = 0; a < 3 && !empty; ++a) {
+        if (d[a] == 0.0) {
+          if (!(s[a] >= lo[a] && s[a] < hi[a])) empty = 1;
+        } else {
+          const double t0 = (lo[a] - s[a]) / d[a], t1 = (hi[a] - s[a]) / d[a];
+          t_lo = fmax(t_lo, fmin(t0, t1));
+          t_hi = fmin(t_hi, fmax(t0, t1));
+        }
+      }
+      if (!empty && t_hi > t_lo) {
+        const double term = L[r] * (t_hi - t_lo);
+        acc += grad_out[r] * term;
+        acc_abs += fabs(grad_out[r]) * term;
+      }
+    }
+    out[q] = acc;
+    out_abs[q] = acc_abs;
+  }
+  free(S);
+  free(Dv);
+  free(L);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Volume ingest: HU -> attenuation, and 16-bit storage rounding.            */
 /* ------------------------------------------------------------------------- */
