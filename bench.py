@@ -310,7 +310,7 @@ def plain_fifo_server(drr, reqs, arrivals, h_rot=1e-3, h_trans=1e-2):
                     "queue replayed (an unstable queue's latencies grow with the run length)"}
 
 
-def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=600, loads=(0.25, 0.5, 0.8, 0.95)):
+def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25, 0.5, 0.8, 0.95)):
     """Served latency: saturation throughput, then Poisson arrivals at fractions of it."""
     import threading
     from paper_2208_12737_gb300 import inputs
@@ -335,11 +335,13 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=600, loads=(0.25, 
             t.wait(120000)
             lat.append(t.result.latency_ms)
 
-    # saturation: everything queued at once; the median of three passes over the same requests
+    # saturation: everything queued at once; after one untimed pass, the median of
+    # three timed passes over the same requests
     reqs = [make_req() for _ in range(sat_requests)]
     srv = drr.Server(device_budget=2 << 30, max_inflight=64, use_cuda_graph=True)
-    for r in reqs[:32]:  # warm-up
+    for r in reqs[:32]:
         srv.submit(*r).wait(120000)
+    drain([srv.submit(*r) for r in reqs], [])
     rates, lat_sat = [], []
     for _ in range(3):
         t0 = time.perf_counter()

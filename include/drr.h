@@ -254,7 +254,9 @@ drr_status drr_probe_l2_read(const void* buf_dev, size_t bytes, int32_t reps, fl
 typedef struct {
   size_t device_budget_bytes; /* device memory reserved for request buffers; 0 -> 512 MiB */
   size_t host_budget_bytes;   /* pinned host staging; 0 -> the device budget */
-  int32_t max_inflight;       /* requests admitted at once (slots); 0 -> 64 */
+  int32_t max_inflight;       /* requests admitted at once (slots); 0 -> 64.  One tick takes at
+                                 most half of the slots and half of each budget (a request that
+                                 needs more goes alone), so the next tick can queue behind it */
   int32_t max_tick_poses;     /* poses packed into one tick; 0 -> 4096 (also the largest B accepted) */
   int32_t use_cuda_graph;     /* nonzero: replay the tick's three launches from a captured graph */
   int32_t device;             /* CUDA device ordinal; -1 -> the current device */

@@ -6,10 +6,13 @@
 // ray-walk and one gradient-finalise launch covering all of their rays; the
 // three launches can be replayed from a CUDA graph captured at start-up (the
 // kernels read the tick's size from a device-resident table).  Up to two ticks
-// are in flight on the server's stream, so requests that arrive while a tick is
-// running are admitted into the next one.  A host function enqueued after each
-// tick's copies marks it finished; the loop then writes results into the
-// callers' buffers, frees the tick's memory and wakes the waiters.
+// are in flight, so requests that arrive while a tick is running are admitted
+// into the next one.  Inputs go up on one copy stream and results come down on
+// another, ordered against the kernels' stream by events, so a tick's copies
+// overlap the neighbouring ticks' kernels.  A host function enqueued after each
+// tick's result copies marks it finished; the loop then writes results into
+// the callers' buffers (without the server lock, so submissions go on),
+// frees the tick's memory and wakes the waiters.
 //
 // Nothing on the device waits on the host: there are no spin loops in the
 // kernels, so a stalled client cannot hang the GPU.
@@ -68,7 +71,8 @@ struct Tick {
   int64_t id = 0;
   int set = 0;
   std::vector<Req*> reqs;
-  cudaEvent_t start = nullptr, stop = nullptr;
+  cudaEvent_t start = nullptr, stop = nullptr;  // around the kernels; stop also orders the result copies
+  cudaEvent_t in_ready = nullptr;               // the tick's inputs are on the device
   std::atomic<bool> done{false};
   struct drr_server_s* owner = nullptr;
 };
@@ -90,7 +94,9 @@ void size_request(Req& q) {
 struct drr_server_s {
   drr_server_config cfg{};
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // kernels
+  cudaStream_t h2d = nullptr;     // input copies
+  cudaStream_t d2h = nullptr;     // result copies
   char* dev_base = nullptr;
   char* host_base = nullptr;
   drr::OffsetArena* dev_arena = nullptr;
@@ -121,7 +127,9 @@ struct drr_server_s {
 
   void run();
   bool form_tick(std::unique_lock<std::mutex>& lk);
+  void copy_results(Tick* t);
   void finish_tick(Tick* t);
+  void sync_streams();
   cudaError_t launch_kernels(int set);
 };
 
@@ -150,11 +158,22 @@ cudaError_t drr_server_s::launch_kernels(int set) {
 // Admit requests (FIFO) into a new tick and enqueue it.  Called with lk held;
 // drops it while staging inputs and issuing CUDA calls.
 bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
+  // One tick takes at most half of the request slots and half of each memory
+  // budget (a request that needs more goes alone), so that the next tick can
+  // be formed and queued while this one runs.  Without the cap a backlog puts
+  // every slot into one tick, the next tick finds none free until it ends, and
+  // the GPU idles between ticks.
+  const int slot_cap = std::max(1, cfg.max_inflight / 2);
   std::vector<Req*> batch;
   int poses = 0;
-  while (!pending.empty() && admitted + static_cast<int>(batch.size()) < cfg.max_inflight) {
+  size_t tick_dev = 0, tick_host = 0;
+  while (!pending.empty() && admitted + static_cast<int>(batch.size()) < cfg.max_inflight &&
+         static_cast<int>(batch.size()) < slot_cap) {
     Req* q = pending.front();
     if (poses + q->r.B > cfg.max_tick_poses) break;
+    if (!batch.empty() && (tick_dev + q->dev_bytes > cfg.device_budget_bytes / 2 ||
+                           tick_host + q->host_bytes > cfg.host_budget_bytes / 2))
+      break;
     size_t doff = 0, hoff = 0;
     if (!dev_arena->alloc(q->dev_bytes, &doff)) break;
     if (!host_arena->alloc(q->host_bytes, &hoff)) {
@@ -168,6 +187,8 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     q->state = kAdmitted;
     q->t_admit = Clock::now();
     poses += q->r.B;
+    tick_dev += q->dev_bytes;
+    tick_host += q->host_bytes;
     batch.push_back(q);
   }
   if (batch.empty()) return false;
@@ -180,6 +201,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   lk.unlock();
   cudaError_t e = cudaEventCreate(&t->start);
   if (e == cudaSuccess) e = cudaEventCreate(&t->stop);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->in_ready, cudaEventDisableTiming);
 
   // carve the buffers and stage the inputs
   Set& st = sets[t->set];
@@ -228,27 +250,34 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   hdr->total_poses = pose_start;
   hdr->pad_ = 0;
   const size_t tbytes = sizeof(drr::ServeHeader) + batch.size() * sizeof(drr::ServeRequest);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(st.d_table, st.h_table, tbytes, cudaMemcpyHostToDevice, stream);
+  // The table set and the request buffers written here belong to no tick still
+  // in flight: this tick's set was last used two ticks ago, which has finished
+  // (its result copies, after its kernels, are done), and the arenas hand out
+  // only memory of finished ticks.
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st.d_table, st.h_table, tbytes, cudaMemcpyHostToDevice, h2d);
   for (Req* q : batch) {
     if (e != cudaSuccess) break;
-    e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->r.B) * 6 * 4, cudaMemcpyHostToDevice, stream);
+    e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->r.B) * 6 * 4, cudaMemcpyHostToDevice, h2d);
     if (e == cudaSuccess && q->grad)
-      e = cudaMemcpyAsync(q->d_grad, q->h_grad, size_t(q->r.B) * q->npix * 4, cudaMemcpyHostToDevice, stream);
+      e = cudaMemcpyAsync(q->d_grad, q->h_grad, size_t(q->r.B) * q->npix * 4, cudaMemcpyHostToDevice, h2d);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(t->in_ready, h2d);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, t->in_ready, 0);
   if (e == cudaSuccess) e = cudaEventRecord(t->start, stream);
   if (e == cudaSuccess) e = launch_kernels(t->set);
   if (e == cudaSuccess) drr::count_launches(3);
   if (e == cudaSuccess) e = cudaEventRecord(t->stop, stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, t->stop, 0);
   for (Req* q : batch) {
     if (e != cudaSuccess) break;
-    e = cudaMemcpyAsync(q->h_out, q->d_out, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, stream);
+    e = cudaMemcpyAsync(q->h_out, q->d_out, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, d2h);
     if (e == cudaSuccess && q->grad)
-      e = cudaMemcpyAsync(q->h_gpose, q->d_gpose, size_t(q->r.B) * 6 * 4, cudaMemcpyDeviceToHost, stream);
+      e = cudaMemcpyAsync(q->h_gpose, q->d_gpose, size_t(q->r.B) * 6 * 4, cudaMemcpyDeviceToHost, d2h);
   }
-  if (e == cudaSuccess) e = cudaLaunchHostFunc(stream, tick_done, t);
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(d2h, tick_done, t);
   if (e != cudaSuccess) {
     // the tick could not be enqueued completely: let what was queued drain, then fail its requests
-    cudaStreamSynchronize(stream);
+    sync_streams();
     for (Req* q : batch) q->status = drr::cuda_error(e, "serving tick");
     if (t->stop) cudaEventDestroy(t->stop);
     t->stop = nullptr;
@@ -260,7 +289,24 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   return true;
 }
 
-// Called with the lock held once the tick's device work and copies are done.
+void drr_server_s::sync_streams() {
+  cudaStreamSynchronize(h2d);
+  cudaStreamSynchronize(stream);
+  cudaStreamSynchronize(d2h);
+}
+
+// Called WITHOUT the lock once the tick's device work and copies are done: the
+// tick is off the in-flight list and its requests are admitted (not done), so
+// no other thread touches them or their callers' buffers meanwhile.
+void drr_server_s::copy_results(Tick* t) {
+  for (Req* q : t->reqs) {
+    if (q->status != DRR_OK) continue;
+    std::memcpy(q->r.drr_out, q->h_out, size_t(q->r.B) * q->npix * 4);
+    if (q->grad) std::memcpy(q->r.grad_pose_out, q->h_gpose, size_t(q->r.B) * 6 * 4);
+  }
+}
+
+// Called with the lock held after copy_results.
 void drr_server_s::finish_tick(Tick* t) {
   if (t->start && t->stop) {
     float ms = 0.f;
@@ -268,10 +314,9 @@ void drr_server_s::finish_tick(Tick* t) {
   }
   if (t->start) cudaEventDestroy(t->start);
   if (t->stop) cudaEventDestroy(t->stop);
+  if (t->in_ready) cudaEventDestroy(t->in_ready);
   for (Req* q : t->reqs) {
     if (q->status == DRR_OK) {
-      std::memcpy(q->r.drr_out, q->h_out, size_t(q->r.B) * q->npix * 4);
-      if (q->grad) std::memcpy(q->r.grad_pose_out, q->h_gpose, size_t(q->r.B) * 6 * 4);
       ++completed;
     } else {
       ++failed;
@@ -296,6 +341,9 @@ void drr_server_s::run() {
     while (!inflight.empty() && inflight.front()->done.load()) {
       Tick* t = inflight.front();
       inflight.pop_front();
+      lk.unlock();
+      copy_results(t);
+      lk.lock();
       finish_tick(t);
     }
     if (stop && inflight.empty()) break;
@@ -329,6 +377,8 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
   if (cfg.device >= 0) e = cudaSetDevice(cfg.device);
   if (e == cudaSuccess) e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_base), cfg.device_budget_bytes);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_base), cfg.host_budget_bytes, 0);
   s->table_bytes = sizeof(drr::ServeHeader) + size_t(cfg.max_inflight) * sizeof(drr::ServeRequest);
@@ -363,6 +413,8 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
     if (s->dev_base) cudaFree(s->dev_base);
     if (s->host_base) cudaFreeHost(s->host_base);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->h2d) cudaStreamDestroy(s->h2d);
+    if (s->d2h) cudaStreamDestroy(s->d2h);
     delete s;
     return st;
   }
@@ -521,7 +573,7 @@ drr_status drr_server_destroy(drr_server s) {
   s->cv_loop.notify_all();
   s->cv_done.notify_all();
   if (s->loop.joinable()) s->loop.join();
-  cudaStreamSynchronize(s->stream);
+  s->sync_streams();
   for (auto& kv : s->reqs) delete kv.second;
   s->reqs.clear();
   for (auto& st : s->sets) {
@@ -533,6 +585,8 @@ drr_status drr_server_destroy(drr_server s) {
   cudaFree(s->dev_base);
   cudaFreeHost(s->host_base);
   cudaStreamDestroy(s->stream);
+  cudaStreamDestroy(s->h2d);
+  cudaStreamDestroy(s->d2h);
   delete s->dev_arena;
   delete s->host_arena;
   delete s;
