@@ -180,3 +180,24 @@ def test_destroy_with_queued_requests(drr, vols):
     tickets = [srv.submit(vol, det, inputs.random_poses(2, seed=100 + i)) for i in range(10)]
     srv.close()  # drains what runs, cancels what waits
     assert True
+
+
+def test_backlog_is_split_between_two_ticks(drr, vols):
+    # A backlog of small requests: no tick takes more than half of the request
+    # slots, so that the next tick can be formed while one runs; results are
+    # those of the direct calls.
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 24, 20, 1.5, 1.5)
+    srv = drr.Server(device_budget=64 << 20, max_inflight=16)
+    srv.pause(True)
+    poses = [inputs.random_poses(1, seed=300 + i) for i in range(40)]
+    tickets = [srv.submit(vol, det, p) for p in poses]
+    srv.pause(False)
+    outs = [t.wait(20000)[0] for t in tickets]
+    per_tick = {}
+    for t in tickets:
+        per_tick[t.result.tick] = per_tick.get(t.result.tick, 0) + 1
+    assert max(per_tick.values()) <= 8 and len(per_tick) >= 5, per_tick
+    for i in (0, 17, 39):
+        np.testing.assert_array_equal(outs[i], _direct(drr, vol, det, poses[i])[0])
+    srv.close()
