@@ -41,6 +41,14 @@ def test_largest_pose_batch(drr):
     G = drr.render_backward(vol, det, torch.from_numpy(poses_np).cuda(), g).cpu().numpy()
     G_ref = oracle.pose_grad(ovol(vol_np, sp), odet(det), poses_np[idx], g.cpu().numpy()[idx].astype(np.float64))
     assert grad_err(G[idx], G_ref).max() < GRAD_TOL, grad_err(G[idx], G_ref)
+    # back-projection of the largest batch (its own 4x8 warp tiles): a non-negative
+    # upstream gradient, so the ~10^4 FP32 adds per voxel do not cancel
+    g_pos = np.random.default_rng(88).uniform(0.0, 1.0, (B, 2, 3))
+    gv = torch.zeros(vol_np.shape, device="cuda")
+    drr.render_backward(vol, det, torch.from_numpy(poses_np).cuda(), torch.from_numpy(g_pos.astype(np.float32)).cuda(),
+                        pose_grad=False, grad_volume=gv)
+    ref = oracle.backproject(vol_np.shape, osp(sp), odet(det), poses_np, g_pos.astype(np.float32).astype(np.float64))
+    np.testing.assert_allclose(gv.cpu().numpy(), ref, rtol=1e-4, atol=1e-6 * np.abs(ref).max())
     with pytest.raises(drr.DrrError):
         drr.render(vol, det, torch.zeros((65536, 6), device="cuda"))
 
@@ -57,6 +65,14 @@ def test_large_detector(drr):
     pix = np.concatenate([pix, [0, det.width - 1, det.height * det.width - 1]])
     E_ref = oracle.render(ovol(vol_np, sp), odet(det), poses_np, pixels=pix)
     assert rel_err(E.reshape(1, -1)[:, pix], E_ref).max() < FP32_TOL
+    # back-projection over all 16.8 M rays: <g, A V> = <A^T g, V>, with g >= 0 so
+    # that the ~10^5 FP32 atomic adds per voxel do not cancel
+    g = torch.rand((1, det.height, det.width), device="cuda", generator=torch.Generator("cuda").manual_seed(89))
+    gv = torch.zeros(vol_np.shape, device="cuda")
+    drr.render_backward(vol, det, torch.from_numpy(poses_np).cuda(), g, pose_grad=False, grad_volume=gv)
+    lhs = float((g.double() * torch.from_numpy(E).cuda().double()).sum())
+    rhs = float((gv.double() * torch.from_numpy(vol_np).cuda().double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * lhs, (lhs, rhs)
 
 
 def test_long_rays(drr):
