@@ -1283,19 +1283,50 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(kJacThread
   }
 }
 
-// Fixed-order FP64 sum of the per-block partials: one warp per pose.
-__global__ void pose_grad_finalize_kernel(const float* __restrict__ partials, int nblk, int ncol,
-                                          float* __restrict__ grad) {
-  grid_dep_wait();
-  const int b = blockIdx.x, lane = threadIdx.x;
-  for (int k = 0; k < ncol; ++k) {
-    double s = 0.0;
-    for (int c = lane; c < nblk; c += 32)
-      s += static_cast<double>(partials[(static_cast<size_t>(b) * nblk + c) * ncol + k]);
+// Fixed-order FP64 sum of one pose's per-tile partial sums (nt tiles, ncol
+// values each, tile-major): thread t adds tiles t, t + kFinThreads, ... in
+// order (one coalesced pass for all columns), each warp's sums are combined by
+// a fixed shuffle tree, and thread k adds the warps' sums of column k in warp
+// order.  The order depends only on nt, so the result is bitwise reproducible,
+// and the server and the direct calls, which both finish through here, agree
+// bit for bit.  Called by all threads of the block.
+constexpr int kFinThreads = 256;
+
+__device__ __forceinline__ void sum_pose_partials(const float* __restrict__ p, int nt, int ncol,
+                                                  float* __restrict__ out) {
+  __shared__ double wsum[kFinThreads / 32][6];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int c = t; c < nt; c += kFinThreads) {
+    const float* row = p + static_cast<size_t>(c) * ncol;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) grad[ncol * b + k] = static_cast<float>(s);
+    for (int k = 0; k < 6; ++k)
+      if (k < ncol) s[k] += static_cast<double>(row[k]);
   }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) wsum[warp][k] = s[k];
+  }
+  __syncthreads();
+  if (t < ncol) {
+    double a = 0.0;
+#pragma unroll
+    for (int w = 0; w < kFinThreads / 32; ++w) a += wsum[w][t];
+    out[t] = static_cast<float>(a);
+  }
+  __syncthreads();  // wsum is reused by the block's next pose
+}
+
+__global__ void __launch_bounds__(kFinThreads) pose_grad_finalize_kernel(const float* __restrict__ partials, int nblk,
+                                                                         int ncol, float* __restrict__ grad) {
+  grid_dep_wait();
+  const int b = blockIdx.x;
+  sum_pose_partials(partials + static_cast<size_t>(b) * nblk * ncol, nblk, ncol, grad + static_cast<size_t>(ncol) * b);
 }
 
 // ---------------------------------------------------------------------------
@@ -1459,23 +1490,18 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
   }
 }
 
-// Fixed-order FP64 sum of each gradient request's per-tile partials: one warp per pose.
-__global__ void serve_finalize_kernel(const ServeHeader* __restrict__ hdr, const ServeRequest* __restrict__ reqs) {
+// Each gradient request's pose gradients from its per-tile partials: one block
+// per pose, summed in the fixed order of sum_pose_partials.
+__global__ void __launch_bounds__(kFinThreads) serve_finalize_kernel(const ServeHeader* __restrict__ hdr,
+                                                                     const ServeRequest* __restrict__ reqs) {
   const int nreq = hdr->nreq, total = hdr->total_poses;
-  const int lane = threadIdx.x & 31;
   for (int i = blockIdx.x; i < total; i += gridDim.x) {
     const int r = find_request(reqs, nreq, i, false);
     const ServeRequest& q = reqs[r];
-    if (q.grad == nullptr) continue;
+    if (q.grad == nullptr) continue;  // uniform across the block
     const int b = i - q.pose_start;
     const int nt = pose_tiles(q.det);
-    for (int k = 0; k < 6; ++k) {
-      double s = 0.0;
-      for (int c = lane; c < nt; c += 32) s += static_cast<double>(q.partials[(static_cast<size_t>(b) * nt + c) * 6 + k]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) q.grad_pose[6 * b + k] = static_cast<float>(s);
-    }
+    sum_pose_partials(q.partials + static_cast<size_t>(b) * nt * 6, nt, 6, q.grad_pose + 6 * b);
   }
 }
 
@@ -1672,14 +1698,14 @@ cudaError_t launch_count_segments(const VolumeDev& vd, const DetDev& det, const 
 }
 
 cudaError_t launch_pose_grad_finalize(const float* partials, int B, int nblk, float* grad_pose, cudaStream_t stream) {
-  return launch_pdl(pose_grad_finalize_kernel, dim3(B), dim3(32), stream, partials, nblk, 6, grad_pose);
+  return launch_pdl(pose_grad_finalize_kernel, dim3(B), dim3(kFinThreads), stream, partials, nblk, 6, grad_pose);
 }
 
 cudaError_t launch_geometry_grad(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B,
                                  const float* grad_drr, float* partials, float* grad_geometry, cudaStream_t stream) {
   cudaError_t e = launch_siddon<kGeoGrad>(vd, det, pg, B, nullptr, nullptr, grad_drr, partials, nullptr, stream);
   if (e != cudaSuccess) return e;
-  return launch_pdl(pose_grad_finalize_kernel, dim3(B), dim3(32), stream, static_cast<const float*>(partials),
+  return launch_pdl(pose_grad_finalize_kernel, dim3(B), dim3(kFinThreads), stream, static_cast<const float*>(partials),
                     pose_tiles(det), 3, grad_geometry);
 }
 
@@ -1699,9 +1725,12 @@ cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, 
                               int walk_grid, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
-  serve_setup_kernel<<<max(1, min(max_poses, 4096)), 32, 0, stream>>>(hdr, reqs);
+  // setup and finalize stride over the tick's poses: one block per pose up to
+  // the walk's grid, so that a small tick does not pay for thousands of idle blocks
+  const int aux = max(1, min(max_poses, walk_grid));
+  serve_setup_kernel<<<aux, 32, 0, stream>>>(hdr, reqs);
   serve_walk_kernel<<<walk_grid, kThreads, 0, stream>>>(hdr, reqs, counter);
-  serve_finalize_kernel<<<max(1, min(max_poses, 4096)), 32, 0, stream>>>(hdr, reqs);
+  serve_finalize_kernel<<<aux, kFinThreads, 0, stream>>>(hdr, reqs);
   return cudaGetLastError();
 }
 
