@@ -163,23 +163,30 @@ def workload_inputs(rank=0):
     return cfg, hu, poses, g
 
 
+_ORACLE_CTX = {}
+
+
 def cpu_oracle_sample(cfg, hu, poses, seconds_target=10.0, threads=0):
-    """Time the FP64 oracle (forward + per-ray pose Jacobian) on a bounded pixel sample."""
+    """Time the FP64 oracle (forward + per-ray pose Jacobian) on a bounded pixel sample.
+    The oracle's volume and a calibration of its ray rate are prepared once per workload."""
     import oracle
     from paper_2208_12737_gb300 import inputs
-    f32 = lambda x: float(np.float32(x))
-    mu = oracle.hu_to_mu(hu, inputs.MU_WATER).astype(np.float32)
-    ov = oracle.Volume(mu, tuple(f32(s) for s in cfg["spacing"]))
     d = cfg["detector"]
-    det = (f32(d.sdr), d.height, d.width, f32(d.delta_h), f32(d.delta_w))
-    rng = np.random.default_rng(123)
     cores = threads if threads > 0 else (os.cpu_count() or 1)
-    # calibrate on a small sample, then size the timed sample to about seconds_target
-    npix = 64
-    t0 = time.perf_counter()
-    oracle.render(ov, det, poses, pixels=rng.integers(0, d.height * d.width, npix), jacobian=True, threads=cores)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    rate = poses.shape[0] * npix / dt
+    key = (cfg["name"], id(hu), cores)
+    if key not in _ORACLE_CTX:
+        f32 = lambda x: float(np.float32(x))
+        mu = oracle.hu_to_mu(hu, inputs.MU_WATER).astype(np.float32)
+        ov = oracle.Volume(mu, tuple(f32(s) for s in cfg["spacing"]))
+        det = (f32(d.sdr), d.height, d.width, f32(d.delta_h), f32(d.delta_w))
+        # calibrate on a small sample, then size each timed sample to about seconds_target
+        npix = 64
+        cal = np.random.default_rng(122).integers(0, d.height * d.width, npix)
+        t0 = time.perf_counter()
+        oracle.render(ov, det, poses, pixels=cal, jacobian=True, threads=cores)
+        dt = max(time.perf_counter() - t0, 1e-3)
+        _ORACLE_CTX[key] = (ov, det, poses.shape[0] * npix / dt, np.random.default_rng(123))
+    ov, det, rate, rng = _ORACLE_CTX[key]
     npix = int(min(d.height * d.width, max(64, rate * seconds_target / poses.shape[0])))
     pix = rng.choice(d.height * d.width, size=npix, replace=False)
     t0 = time.perf_counter()
@@ -199,7 +206,8 @@ def run_reference(args, rank, world):
     per = []
     base = None
     for i in range(args.warmup + args.steps):
-        cb, dt, rays = cpu_oracle_sample(cfg, hu, poses, seconds_target=max(1.0, 60.0 / (args.steps + args.warmup)))
+        # each step a bounded sample: the whole run is about 90 s of oracle work for any K and W
+        cb, dt, rays = cpu_oracle_sample(cfg, hu, poses, seconds_target=max(0.02, 90.0 / (args.steps + args.warmup)))
         if i >= args.warmup:
             per.append(cb["value"])
             base = cb
