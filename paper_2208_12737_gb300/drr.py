@@ -564,18 +564,60 @@ def _autograd():
             g = render_backward(ctx.volume, ctx.det, poses.contiguous(), grad.contiguous().float(), jac=J)
             return g, None, None
 
-    return DRRFunction
+    class DRRVolumeFunction(torch.autograd.Function):
+        """(mu (nz, ny, nx), poses (B, 6)) -> DRR (B, H, W).  E is linear in the volume
+        (Eq. 2), so dL/d mu is the back-projection of dL/dE (the transpose of the forward
+        map); dL/d poses comes from the fused Jacobian.  Each is computed only if needed."""
+
+        @staticmethod
+        def forward(ctx, mu, poses, spacing, det):
+            vol = Volume(mu.detach(), spacing)  # device-to-device copy into the padded layout
+            poses = poses.contiguous()
+            if ctx.needs_input_grad[1]:
+                E, J = render(vol, det, poses, jacobian=True)
+            else:
+                E, J = render(vol, det, poses), None
+            ctx.volume = vol
+            ctx.det = det
+            ctx.save_for_backward(poses, J)
+            return E
+
+        @staticmethod
+        def backward(ctx, grad):
+            poses, J = ctx.saved_tensors
+            g = grad.contiguous().float()
+            g_mu = g_pose = None
+            if ctx.needs_input_grad[1]:
+                g_pose = render_backward(ctx.volume, ctx.det, poses, g, jac=J)
+            if ctx.needs_input_grad[0]:
+                g_mu = torch.zeros(ctx.volume.shape_zyx, device=g.device, dtype=torch.float32)
+                render_backward(ctx.volume, ctx.det, poses, g, pose_grad=False, grad_volume=g_mu)
+            return g_mu, g_pose, None, None
+
+    return DRRFunction, DRRVolumeFunction
 
 
 _fn = None
+_vfn = None
 
 
 def drr(volume: Volume, det, poses):
     """Differentiable DRR: E = drr(volume, det, poses) with gradients to poses."""
-    global _fn
+    global _fn, _vfn
     if _fn is None:
-        _fn = _autograd()
+        _fn, _vfn = _autograd()
     return _fn.apply(poses, volume, det)
+
+
+def drr_volume(mu, spacing, det, poses):
+    """Differentiable DRR of a volume held as a tensor: E = drr_volume(mu, spacing, det, poses)
+    with mu a (nz, ny, nx) FP32 CUDA tensor of attenuation (/mm); gradients flow to mu (by
+    the back-projection) and to poses, whichever requires them.  The volume is copied into
+    the library's padded layout on every call."""
+    global _fn, _vfn
+    if _fn is None:
+        _fn, _vfn = _autograd()
+    return _vfn.apply(mu, poses, tuple(float(x) for x in spacing), det)
 
 
 class DRR:

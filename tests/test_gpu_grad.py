@@ -244,3 +244,33 @@ def test_backprojection_ct_full_size_sampled_voxels(drr):
     err = np.abs(got - ref)
     assert np.all(err <= 2e-5 * ref_abs + 1e-30), (err / np.maximum(ref_abs, 1e-30)).max()
     assert np.all(got[ref_abs == 0] == 0)
+
+
+def test_autograd_through_volume_and_poses(drr):
+    # drr_volume: a volume held as a tensor; a linear loss sum(w * E) has dL/d mu = A^T w
+    # (the oracle's back-projector) and dL/d poses = sum(w * dE/d eta) (its analytic gradient)
+    rng = np.random.default_rng(66)
+    shape, sp = (10, 12, 14), (1.1, 0.9, 1.3)
+    det = inputs.Detector(70.0, 11, 9, 1.4, 1.5)
+    poses_np = inputs.random_poses(2, seed=67)
+    mu_np = rng.uniform(0, 0.05, shape).astype(np.float32)
+    w_np = inputs.upstream_grad((2, 11, 9), seed=68)
+    w = torch.from_numpy(w_np).cuda()
+    mu = torch.from_numpy(mu_np).cuda().requires_grad_(True)
+    P = torch.from_numpy(poses_np).cuda().requires_grad_(True)
+    E = drr.drr_volume(mu, sp, det, P)
+    E_ref = oracle.render(ovol(mu_np, sp), odet(det), poses_np)
+    assert rel_err(E.detach().cpu().numpy(), E_ref).max() < FP32_TOL
+    (E * w).sum().backward()
+    ref_mu = oracle.backproject(shape, osp(sp), odet(det), poses_np, w_np.astype(np.float64))
+    np.testing.assert_allclose(mu.grad.cpu().numpy(), ref_mu, atol=2e-5 * np.abs(ref_mu).max())
+    G_ref = oracle.pose_grad(ovol(mu_np, sp), odet(det), poses_np, w_np.astype(np.float64))
+    assert grad_err(P.grad.cpu().numpy(), G_ref).max() < GRAD_TOL
+    # the volume alone (poses without grad): the forward walk, then the back-projection
+    mu2 = torch.from_numpy(mu_np).cuda().requires_grad_(True)
+    (drr.drr_volume(mu2, sp, det, torch.from_numpy(poses_np).cuda()) * w).sum().backward()
+    np.testing.assert_allclose(mu2.grad.cpu().numpy(), ref_mu, atol=2e-5 * np.abs(ref_mu).max())
+    # the poses alone (a constant volume tensor): no back-projection
+    P3 = torch.from_numpy(poses_np).cuda().requires_grad_(True)
+    (drr.drr_volume(torch.from_numpy(mu_np).cuda(), sp, det, P3) * w).sum().backward()
+    assert torch.equal(P3.grad, P.grad)
