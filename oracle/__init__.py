@@ -84,6 +84,8 @@ def _load():
                                            ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32,
                                            _dp, _dp]
         lib.oracle_backproject.restype = ctypes.c_int
+        lib.oracle_backproject_ray.argtypes = [_ip, _dp, _dp, _dp, ctypes.c_double, _dp]
+        lib.oracle_backproject_ray.restype = ctypes.c_int
         lib.oracle_voxel_adjoint.argtypes = [_ip, _dp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_double, ctypes.c_double, _fp, ctypes.c_int32, _dp,
                                              _i64p, ctypes.c_int64, _dp, _dp]
@@ -258,6 +260,21 @@ def backproject(shape_zyx, spacing, det, poses, grad_out):
     lib.oracle_backproject(_ptr(n, ctypes.c_int32), _ptr(delta, ctypes.c_double), float(sdr), int(H), int(W),
                            float(dh), float(dw), _ptr(poses, ctypes.c_float), int(B), _ptr(g, ctypes.c_double),
                            _ptr(out, ctypes.c_double))
+    return out
+
+
+def backproject_ray(shape_zyx, spacing, s, p, g: float = 1.0):
+    """Transpose of V -> E for the single ray s -> p: (nz, ny, nx) float64, g |p - s| times
+    each Siddon segment's length (in alpha) in its voxel (Eq. 2 read as linear in V)."""
+    lib = _load()
+    nz, ny, nx = shape_zyx
+    n = np.array([nx, ny, nz], dtype=np.int32)
+    delta = np.array(spacing, dtype=np.float64)
+    s = _c(s, np.float64)
+    p = _c(p, np.float64)
+    out = np.zeros((nz, ny, nx))
+    lib.oracle_backproject_ray(_ptr(n, ctypes.c_int32), _ptr(delta, ctypes.c_double), _ptr(s, ctypes.c_double),
+                               _ptr(p, ctypes.c_double), float(g), _ptr(out, ctypes.c_double))
     return out
 
 

@@ -489,6 +489,18 @@ int oracle_backproject(const int32_t n[3], const double delta[3], double sdr, in
   return 0;
 }
 
+/* The transpose of V -> E for one ray s -> p: grad_vol[z][y][x] += g * |p - s| *
+ * (length in alpha of each Siddon segment in that voxel). */
+int oracle_backproject_ray(const int32_t n[3], const double delta[3], const double s[3], const double p[3],
+                           double g, double* grad_vol) {
+  crossing_t* list = alloc_list(n);
+  const double L = sqrt((p[0] - s[0]) * (p[0] - s[0]) + (p[1] - s[1]) * (p[1] - s[1]) + (p[2] - s[2]) * (p[2] - s[2]));
+  bp_ctx_t ctx = {n, grad_vol, g * L};
+  siddon_ray(n, delta, NULL, s, p, NULL, NULL, list, bp_add, &ctx);
+  free(list);
+  return 0;
+}
+
 /* The transpose of V -> E at selected voxels, straight from its definition
  * (Eq. 1 with a piecewise-constant volume is linear in V): the adjoint at voxel
  * v is the sum over all rays of g * |p - s| * (the length, in alpha, of the

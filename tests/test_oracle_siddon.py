@@ -21,6 +21,23 @@ def test_worked_examples(golden):
             assert abs(E - L * ex["F"]) <= 1e-12 * L * ex["F"], ex["name"]
 
 
+def test_worked_backprojection(golden):
+    # the transpose of V -> E for a single worked ray, derived by hand from the same segments
+    V = np.array(golden["volume_zyx"], dtype=np.float64)
+    done = 0
+    for ex in golden["examples"]:
+        if "backprojection_g1" not in ex:
+            continue
+        bt = oracle.backproject_ray(V.shape, golden["spacing"], ex["s"], ex["p"], 1.0)
+        want = np.array(ex["backprojection_g1"])
+        np.testing.assert_allclose(bt, want, rtol=0, atol=1e-12 * np.abs(want).max(), err_msg=ex["name"])
+        # adjoint of the worked forward value: <A^T 1, V> = E
+        E = oracle.siddon_ray(_vol(golden), ex["s"], ex["p"])
+        assert abs(np.sum(bt * V) - E) <= 1e-12 * abs(E), ex["name"]
+        done += 1
+    assert done == 2
+
+
 def test_worked_gradient(golden):
     V = _vol(golden)
     ex = [e for e in golden["examples"] if e["name"] == "generic"][0]
