@@ -117,6 +117,63 @@ def job_throughput(world, rays_per_rank, ms):
     return world * rays_per_rank / (ms * 1e-3) / 1e9
 
 
+def timed_steps(fn, k, before=None, clock="cuda"):
+    """Run fn k times and return the duration of each call in ms.  clock="cuda":
+    CUDA events recorded on the current stream around each call (after an
+    untimed `before()`, e.g. an L2 flush); clock="host": perf_counter around
+    each call (the CPU stand-in used by the multi-process tests)."""
+    if clock == "host":
+        out = []
+        for i in range(k):
+            if before is not None:
+                before(i)
+            t0 = time.perf_counter()
+            fn()
+            out.append((time.perf_counter() - t0) * 1e3)
+        return out
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    for i in range(k):
+        if before is not None:
+            before(i)
+        starts[i].record()
+        fn()
+        ends[i].record()
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def job_timing(world, rays_per_rank, per_rank_ms, dist=None, device=None):
+    """Whole-job figures from each rank's mean step times (a list, one entry per
+    timed quantity): the slowest rank sets every time, and the throughput counts
+    the rays of all ranks.  Returns (max-over-ranks ms list, throughput list)."""
+    ms = max_over_ranks([statistics.mean(x) for x in per_rank_ms], dist, device)
+    return ms, [job_throughput(world, rays_per_rank, m) for m in ms]
+
+
+def resolve_world(gpus, env=None):
+    """(rank, world, local_rank) of this process.  A run with --gpus N > 1 must be
+    launched one process per GPU (torchrun --nproc-per-node N), which sets
+    WORLD_SIZE = N; anything else is an error, so a multi-GPU run can never
+    print a one-rank number."""
+    env = os.environ if env is None else env
+    if gpus < 1:
+        raise SystemExit("bench.py: --gpus must be >= 1")
+    if "WORLD_SIZE" in env:
+        world = int(env["WORLD_SIZE"])
+        if world != gpus:
+            raise SystemExit(f"bench.py: --gpus {gpus} but WORLD_SIZE={world}: launch one process per GPU "
+                             f"with torchrun --nproc-per-node {gpus}")
+    elif gpus > 1:
+        raise SystemExit(f"bench.py: --gpus {gpus} needs one process per GPU: run it as "
+                         f"python -m torch.distributed.run --nproc-per-node {gpus} --master-addr 127.0.0.1 "
+                         f"bench.py --gpus {gpus} ...")
+    else:
+        world = 1
+    return int(env.get("RANK", "0")), world, int(env.get("LOCAL_RANK", "0"))
+
+
 def kernel_source_hash():
     """sha256 of the walk kernels' sources: a stored ncu traffic figure applies only to this source."""
     import hashlib
@@ -743,15 +800,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     def timed(fn, k):
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
-        for i in range(k):
-            flush.fill_(float(i))
-            starts[i].record()
-            fn()
-            ends[i].record()
-        torch.cuda.synchronize()
-        return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        return timed_steps(fn, k, before=lambda i: flush.fill_(float(i)))
 
     if dist:
         dist.barrier()
@@ -816,23 +865,25 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     drr.profile_reset()
 
-    ms, fms, ems = max_over_ranks([statistics.mean(step_ms), statistics.mean(fwd_ms), statistics.mean(e2e_ms)],
-                                  dist, dev)
+    (ms, fms, ems), (value, fwd_value, e2e_value) = job_timing(world, rays, [step_ms, fwd_ms, e2e_ms], dist, dev)
+    # the gather roofline's L2 ceiling, measured in the same run
+    l2 = l2_read_gbs(drr)
     if dist:
         dist.barrier()
     if rank != 0:
         dist.destroy_process_group()
         return
-    value = job_throughput(world, rays, ms)
     peaks, which = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # dominant kernel: the fused forward + Jacobian walk; algorithmic work per launch
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # dominant kernel: the fused forward + Jacobian walk.  Its algorithmic bytes per
+    # launch are the voxel gathers of Eq. 2, one storage element per segment.
     k_ms = kern_ms / max(kern_n, 1)
+    gather_gbs = seg * elem / (k_ms * 1e-3) / 1e9
     ops_per_seg = 8  # 3-way min (2), length (1), accumulate (1), next crossing (1), Jacobian weight and sums (3)
-    achieved = seg * ops_per_seg / (k_ms * 1e-3) / 1e12
     peak_alu = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lanes x max SM clock, tera-ops/s
-    gather_gbs = seg * elem / (k_ms * 1e-3) / 1e9  # voxel gathers only
     vol_bytes = int(np.prod(hu.shape)) * elem
+    issue = issue_roofline(k_ms, sm_max)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -843,25 +894,37 @@ def run_ours(args, rank, world, local_rank):
                    "segments_per_step": int(seg), "storage": args.storage,
                    "step": "pose setup + fused Siddon fwd with per-ray pose Jacobian + g.J reduction",
                    "l2": "flushed (512 MB write) before every timed step, outside the timed events"},
-        "fwd_only": {"value": job_throughput(world, rays, fms), "unit": UNIT, "ms_per_step": fms},
+        "fwd_only": {"value": fwd_value, "unit": UNIT, "ms_per_step": fms},
         "drrs_per_s": world * B / (ms * 1e-3),
         "segments_per_s": world * seg / (ms * 1e-3),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "Tops/s",
-                     "frac": achieved / peak_alu, "traffic": profiled_traffic("siddon_fwd_jac"),
+        # Gather roofline: voxel bytes gathered per second by the dominant kernel (segments x
+        # element size / its event-timed launch) against the measured HBM copy bandwidth, and
+        # beside it against the L2 read bandwidth probed in this run.  What binds the kernel is
+        # instruction issue (`issue`: ncu warp instructions per launch / launch time / the issue
+        # peak of 4 schedulers x SMs x max clock); the gathers stay well below both ceilings.
+        "roofline": {"bound": "hbm", "achieved": gather_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": gather_gbs / hbm, "traffic": profiled_traffic("siddon_fwd_jac"),
                      "kernel": "siddon_fwd_jac", "kernel_ms": k_ms,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz ({which} sm_max)",
-                     "gathered_gbs": gather_gbs,
-                     # issued warp instructions (ncu count per launch, current source only) per
-                     # second of the event-timed launch, against 4 schedulers x SMs x max clock
-                     "issue": issue_roofline(k_ms, sm_max),
+                     "algorithmic_bytes_per_launch": int(seg) * elem,
+                     "unit_of_work": f"{int(seg)} segments x {elem} B voxel gather",
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({which})",
+                     "l2": {"achieved_gbs": gather_gbs, "peak_gbs": l2, "frac": gather_gbs / l2,
+                            "peak_source": "measured in this run: 64 MB L2-resident buffer streamed with "
+                                           "16-byte L2-only loads (drr_probe_l2_read)"},
+                     "limiter": "issue",
+                     "issue": issue,
+                     # aside: a hand-counted 8 essential FP32 ops per segment against the FP32 lanes
+                     "alu_aside": {"ops_per_segment": ops_per_seg,
+                                   "achieved_tops": seg * ops_per_seg / (k_ms * 1e-3) / 1e12,
+                                   "peak_tops": peak_alu,
+                                   "frac": seg * ops_per_seg / (k_ms * 1e-3) / 1e12 / peak_alu},
                      # the volume's compulsory first touch from HBM after the flush, per kernel launch
                      "compulsory_hbm": {"bytes": vol_bytes, "achieved_gbs": vol_bytes / (k_ms * 1e-3) / 1e9,
-                                        "peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
-                                        "frac": vol_bytes / (k_ms * 1e-3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}},
+                                        "peak_gbs": hbm, "frac": vol_bytes / (k_ms * 1e-3) / 1e9 / hbm}},
         "step_ms_stats": {"mean": statistics.mean(step_ms), "median": statistics.median(step_ms),
                           "p99": float(np.quantile(step_ms, 0.99)), "min": min(step_ms), "max": max(step_ms),
                           "rank": rank},
-        "e2e": {"value": job_throughput(world, rays, ems), "unit": UNIT, "h2d_bytes_per_step": B * 6 * 4,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 6 * 4,
                 "d2h_bytes_per_step": B * H * W * 4 + B * 6 * 4},
         "graph_replay": ({"ms_per_step": graph_ms, "value": job_throughput(1, rays, graph_ms), "unit": UNIT}
                          if isinstance(graph_ms, float) else {"unavailable": graph_ms}),
@@ -876,9 +939,6 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": wall,
     }
     if not args.no_baselines:
-        l2 = l2_read_gbs(drr)
-        line["roofline"]["gather"] = {"achieved_gbs": gather_gbs, "peak_gbs": l2, "frac": gather_gbs / l2,
-                                      "peak_source": "measured: 64 MB L2-resident buffer streamed with 16-byte loads"}
         line["fd_baseline"] = fd_baseline(drr, vol, det, poses, rays)
         line["fd_baseline_plain_fp32"] = fd_baseline(drr, vol, det, poses, rays, plain=True)
         line["volume_adjoint"] = adjoint_bench(drr, vol, det, poses, g, hu.shape, rays)
@@ -925,11 +985,9 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the 512^3 precision-sweep workload")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds per served load level")
     args = ap.parse_args()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    rank, world, local_rank = resolve_world(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
