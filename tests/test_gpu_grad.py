@@ -60,9 +60,9 @@ def test_per_ray_jacobian_vs_oracle(drr):
     for grp in (slice(0, 3), slice(3, 6)):
         scale = np.abs(J_ref[:, grp]).max()
         err = np.abs(J[:, grp] - J_ref[:, grp]) / scale
-        # per-ray agreement; a ray passing within rounding distance of a voxel edge is a
-        # kink of E where either one-sided value is correct, so a handful may differ
-        assert np.mean(err < 1e-4) > 0.999, np.sort(err.ravel())[-10:]
+        # every ray: the crossing order is exact, so no ray sits on the other side
+        # of a kink from the oracle (measured worst 5e-7 of the group's largest entry)
+        assert err.max() < GRAD_TOL, np.sort(err.ravel())[-10:]
         assert np.median(err) < 1e-6
 
 
@@ -87,7 +87,7 @@ def test_jacobian_through_near_coincident_crossings(drr):
     J_ref = np.moveaxis(J_ref, -1, 1)
     for grp in (slice(0, 3), slice(3, 6)):
         err = np.abs(J[:, grp] - J_ref[:, grp]) / np.abs(J_ref[:, grp]).max()
-        assert np.mean(err < 1e-4) > 0.999, np.sort(err.ravel())[-10:]
+        assert err.max() < GRAD_TOL, np.sort(err.ravel())[-10:]  # every ray (measured worst 2.3e-7)
     g_np = inputs.upstream_grad((4, 24, 24), seed=62)
     G_ref = oracle.pose_grad(ov, odet(det), poses_np, g_np.astype(np.float64))
     g = torch.from_numpy(g_np).cuda()
@@ -97,7 +97,8 @@ def test_jacobian_through_near_coincident_crossings(drr):
 
 
 def test_ct_full_size_pose_gradient(drr):
-    # the benchmarked workload: 512x512x133, 200x200, 16 poses; oracle on 2 poses
+    # the benchmarked workload (512x512x133, 200x200, 16 poses): the pose gradient of
+    # every pose, from the stored Jacobian and from the re-walk, against the oracle's
     cfg = inputs.CT
     hu = inputs.ct_volume_hu()
     det = cfg["detector"]
@@ -105,13 +106,24 @@ def test_ct_full_size_pose_gradient(drr):
     vol = drr.Volume(hu, cfg["spacing"], hu=True)
     poses = torch.from_numpy(poses_np).cuda()
     g_np = inputs.upstream_grad((cfg["batch"], det.height, det.width), seed=54)
+    g = torch.from_numpy(g_np).cuda()
     E, J = drr.render(vol, det, poses, jacobian=True)
-    G = drr.render_backward(vol, det, poses, torch.from_numpy(g_np).cuda(), jac=J).cpu().numpy()
+    G = drr.render_backward(vol, det, poses, g, jac=J).cpu().numpy()
+    G_walk = drr.render_backward(vol, det, poses, g).cpu().numpy()
     mu = oracle.hu_to_mu(hu, inputs.MU_WATER).astype(np.float32)
-    sel = [0, 7]
-    G_ref = oracle.pose_grad(ovol(mu, cfg["spacing"]), odet(det), poses_np[sel],
-                             g_np[sel].astype(np.float64))
-    assert grad_err(G[sel], G_ref).max() < GRAD_TOL, grad_err(G[sel], G_ref)
+    ov = ovol(mu, cfg["spacing"])
+    G_ref = oracle.pose_grad(ov, odet(det), poses_np, g_np.astype(np.float64))
+    assert G_ref.shape == (cfg["batch"], 6)
+    assert grad_err(G, G_ref).max() < GRAD_TOL, grad_err(G, G_ref)
+    assert grad_err(G_walk, G_ref).max() < GRAD_TOL, grad_err(G_walk, G_ref)
+    # and the stored per-ray Jacobian of all 640,000 rays, element by element
+    E_ref, J_ref = oracle.render(ov, odet(det), poses_np, jacobian=True)
+    assert rel_err(E.cpu().numpy(), E_ref).max() < FP32_TOL
+    J = J.cpu().numpy()
+    J_ref = np.moveaxis(J_ref, -1, 1)
+    for grp in (slice(0, 3), slice(3, 6)):
+        err = np.abs(J[:, grp] - J_ref[:, grp]) / np.abs(J_ref[:, grp]).max()
+        assert err.max() < GRAD_TOL, np.sort(err.ravel())[-10:]  # measured worst 2.8e-6
 
 
 def test_pose_gradient_is_deterministic(drr):
