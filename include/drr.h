@@ -75,16 +75,28 @@ typedef struct {
   float delta_w_mm;
 } drr_detector;
 
+/* Storage layouts of a device-resident volume.  Every layout is padded
+ * linear storage (one zero voxel of padding on each face, so every gather of
+ * the walk is in bounds): a voxel step along any axis moves the walk's offset
+ * by one fixed signed stride.  They differ in which axis is fastest, i.e. in
+ * which neighbouring voxels share a cache sector.  The best choice puts the
+ * axis along which a warp's rays (an 8 x 4 pixel tile, detector columns first)
+ * are spread fastest: for the canonical pose, whose detector columns run
+ * along y, that is DRR_LAYOUT_LINEAR_Y. */
+typedef enum {
+  DRR_LAYOUT_DEFAULT = 0,  /* = DRR_LAYOUT_LINEAR_X */
+  DRR_LAYOUT_LINEAR_X = 1, /* x fastest, then y, then z */
+  DRR_LAYOUT_LINEAR_Y = 2, /* y fastest, then x, then z */
+  DRR_LAYOUT_LINEAR_Z = 3  /* z fastest, then x, then y */
+} drr_layout;
+
 /* Options for drr_volume_create.  Zero-initialised fields take defaults. */
 typedef struct {
   drr_dtype storage;  /* DRR_F32 (default), DRR_BF16 or DRR_F16 */
   float hu_mu_water;  /* attenuation of water in /mm for DRR_I16_HU input:
                          mu = max(0, mu_water (1 + HU/1000)); 0 -> 0.02 */
-  int32_t layout;     /* 0 = default = 1 = padded linear (x fastest, one zero
-                         voxel of padding per face): the only layout; other
-                         values are DRR_ERR_INVALID (a bricked layout adds
-                         per-step work to a walk bound by instruction issue) */
-  int32_t brick[3];   /* reserved, ignored */
+  int32_t layout;     /* a drr_layout; other values are DRR_ERR_INVALID */
+  int32_t brick[3];   /* reserved, must be zero */
 } drr_volume_options;
 
 /* ---- volumes (Sec. 2.2: the CT volume V and its spacing) ---------------- */
@@ -296,16 +308,50 @@ drr_status drr_server_create(const drr_server_config* cfg, drr_server* out);
 drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* ticket);
 /* Wait up to timeout_ms (< 0: forever) for a ticket.  Returns the request's
  * status (DRR_OK, DRR_ERR_CANCELLED, ...) and releases the ticket, or
- * DRR_ERR_TIMEOUT (ticket kept), or DRR_ERR_NOT_FOUND for an unknown ticket. */
+ * DRR_ERR_TIMEOUT (ticket kept), or DRR_ERR_NOT_FOUND for an unknown ticket.
+ * DRR_ERR_DEVICE: a serving kernel found the request's part of the tick table
+ * inconsistent (a decoded pose index outside the request) and set the
+ * request's device status word instead of touching memory; its outputs were
+ * not written.  Several threads may wait at once (on different tickets). */
 drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, drr_result* res);
+
+/* State of a ticket without waiting (no counterpart in the paper). */
+typedef enum {
+  DRR_REQ_QUEUED = 0,  /* submitted, not yet admitted into a tick */
+  DRR_REQ_RUNNING = 1, /* admitted: its tick is on the GPU or its results are being copied */
+  DRR_REQ_DONE = 2     /* finished (any status); drr_server_wait returns at once */
+} drr_request_state;
+/* Non-blocking: *state receives a drr_request_state.  The ticket is kept
+ * (release it with drr_server_wait).  DRR_ERR_NOT_FOUND for an unknown ticket. */
+drr_status drr_server_poll(drr_server s, uint64_t ticket, int32_t* state);
 /* Cancel a request that has not been admitted yet; DRR_ERR_BUSY once it has. */
 drr_status drr_server_cancel(drr_server s, uint64_t ticket);
 drr_status drr_server_get_stats(drr_server s, drr_server_stats* out);
 /* paused != 0: admit no new requests (queued ones wait; ticks already running
  * finish), e.g. to drain the GPU for maintenance.  paused == 0 resumes. */
 drr_status drr_server_pause(drr_server s, int32_t paused);
-/* Finish in-flight ticks, cancel queued requests and free everything. */
+/* Finish in-flight ticks, cancel queued requests and free everything.
+ * Threads blocked in drr_server_wait at the time return first (their requests
+ * finish or are cancelled); no other call on s may start once destroy has. */
 drr_status drr_server_destroy(drr_server s);
+
+/* Fault injection on the host, for tests of the device-status path (no
+ * counterpart in the paper): the queued request's device status word is
+ * uploaded with `bits` set instead of zero, so after its tick the server
+ * reports DRR_ERR_DEVICE for it exactly as if a kernel had flagged it.  No
+ * kernel is given an inconsistent table.  DRR_ERR_BUSY once the request has
+ * been admitted, DRR_ERR_NOT_FOUND for an unknown ticket. */
+drr_status drr_server_inject_device_status(drr_server s, uint64_t ticket, uint32_t bits);
+
+/* Layout of one serving tick (host only, no CUDA call; no counterpart in the
+ * paper): for n admitted requests of B[i] poses on detectors dets[i], in
+ * admission order, request i owns the tick's 8x4-pixel warp tiles
+ * [tile_start[i], tile_start[i] + B[i] * ceil(W/8) * ceil(H/4)) and poses
+ * [pose_start[i], pose_start[i] + B[i]); totals[0] = all tiles, totals[1] =
+ * all poses.  The serving kernels decode tile and pose indices against these
+ * starts.  Exposed so the layout's invariants can be tested on their own. */
+drr_status drr_serve_tick_layout(int32_t n, const int32_t* B, const drr_detector* dets, int32_t* tile_start,
+                                 int32_t* pose_start, int32_t* totals);
 
 /* ---- host-side offset arena (the servers' admission allocator) ----------- */
 /* A first-fit allocator over [0, capacity) with alignment and coalescing; it

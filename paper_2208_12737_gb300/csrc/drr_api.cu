@@ -257,11 +257,15 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
   if (padded >= (int64_t{1} << 31)) return drr::set_error(DRR_ERR_INVALID, "volume too large (padded voxels >= 2^31)");
   drr_dtype storage = DRR_F32;
   float mu_water = 0.02f;
+  int layout = DRR_LAYOUT_LINEAR_X;
   if (opt) {
     storage = opt->storage;
     if (opt->hu_mu_water != 0.f) mu_water = opt->hu_mu_water;
-    if (opt->layout != 0 && opt->layout != 1)
-      return drr::set_error(DRR_ERR_INVALID, "layout %d not supported (0 or 1)", opt->layout);
+    if (opt->layout < 0 || opt->layout > DRR_LAYOUT_LINEAR_Z)
+      return drr::set_error(DRR_ERR_INVALID, "layout %d not supported (0 .. 3)", opt->layout);
+    if (opt->layout != 0) layout = opt->layout;
+    if (opt->brick[0] != 0 || opt->brick[1] != 0 || opt->brick[2] != 0)
+      return drr::set_error(DRR_ERR_INVALID, "brick must be zero: the layouts are padded linear");
   }
   if (storage != DRR_F32 && storage != DRR_BF16 && storage != DRR_F16)
     return drr::set_error(DRR_ERR_INVALID, "storage dtype must be DRR_F32, DRR_BF16 or DRR_F16");
@@ -300,9 +304,17 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
   vd.delta[1] = dy_mm;
   vd.delta[2] = dz_mm;
   vd.dtype = storage == DRR_F32 ? drr::kF32 : storage == DRR_BF16 ? drr::kBF16 : drr::kF16;
-  vd.stride[0] = 1;
-  vd.stride[1] = nx + 2;
-  vd.stride[2] = (nx + 2) * (ny + 2);
+  {
+    // padded linear storage, the layout's axis fastest, the other two in x, y, z order
+    const int fast = layout - DRR_LAYOUT_LINEAR_X;
+    const int order[3] = {fast, fast == 0 ? 1 : 0, fast == 2 ? 1 : 2};
+    int stride = 1;
+    for (int q = 0; q < 3; ++q) {
+      vd.stride[order[q]] = stride;
+      stride *= vd.n[order[q]] + 2;
+    }
+  }
+  v->layout = layout;
   vd.origin = vd.stride[2] + vd.stride[1] + vd.stride[0];
   vd.elems = padded;
   vd.out_scale = 1.f;

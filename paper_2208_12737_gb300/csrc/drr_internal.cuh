@@ -110,6 +110,15 @@ struct ServeHeader {
   int pad_;
 };
 
+// Per-request device status words of a serving tick (one unsigned int per
+// request, after the request table).  The host uploads them as zero; a kernel
+// that meets an inconsistency it can detect sets a bit instead of touching
+// memory, and the host returns DRR_ERR_DEVICE for that request.
+enum ServeStatusBits : unsigned int {
+  kServeTileRange = 1u,  // a tile decoded to a pose index outside its request
+  kServePoseRange = 2u,  // a tick pose index decoded outside its request
+};
+
 // Launchers (drr_kernels.cu).  All enqueue on `stream` and return the
 // cudaGetLastError() of the launch.
 cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, const VolumeDev* vd, PoseGeom* out,
@@ -147,8 +156,8 @@ cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const Pos
 // fixed-order pose-gradient sums.  Grids are fixed so the three launches can be
 // captured once in a CUDA graph; the counts are read from the device header.
 int serve_walk_grid(int device);
-cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, int* counter, int max_poses,
-                              int walk_grid, cudaStream_t stream);
+cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, unsigned int* status, int* counter,
+                              int max_poses, int walk_grid, cudaStream_t stream);
 // Volume ingest.
 cudaError_t launch_abs_max(const void* src, int src_dtype, int64_t count, float mu_water, unsigned int* out_bits,
                            cudaStream_t stream);
@@ -170,6 +179,7 @@ struct drr_volume_s {
   void* storage = nullptr;
   size_t bytes = 0;
   int device = 0;
+  int layout = DRR_LAYOUT_LINEAR_X;
   drr::VolumeDev vd{};
   std::atomic<int> refs{0};  // requests queued or running in servers
 };

@@ -1351,15 +1351,15 @@ __global__ void abs_max_kernel(const void* __restrict__ src, int src_dtype, int6
   if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));
 }
 
+// Element e of the padded storage holds voxel (e / stride_a) mod (n_a + 2) - 1 per
+// axis a, whichever axis the layout makes fastest.
 __global__ void ingest_kernel(const void* __restrict__ src, int src_dtype, float mu_water, VolumeDev vd,
                               void* __restrict__ dst, float scale) {
-  const int px = vd.n[0] + 2, py = vd.n[1] + 2;
   for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < vd.elems;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int pk = static_cast<int>(e / (static_cast<int64_t>(px) * py));
-    const int rem = static_cast<int>(e - static_cast<int64_t>(pk) * px * py);
-    const int pj = rem / px, pi = rem - pj * px;
-    const int i = pi - 1, j = pj - 1, k = pk - 1;
+    const int i = static_cast<int>((e / vd.stride[0]) % (vd.n[0] + 2)) - 1;
+    const int j = static_cast<int>((e / vd.stride[1]) % (vd.n[1] + 2)) - 1;
+    const int k = static_cast<int>((e / vd.stride[2]) % (vd.n[2] + 2)) - 1;
     float v = 0.f;
     if (i >= 0 && j >= 0 && k >= 0 && i < vd.n[0] && j < vd.n[1] && k < vd.n[2])
       v = source_value(src, src_dtype, (static_cast<int64_t>(k) * vd.n[1] + j) * vd.n[0] + i, mu_water);
@@ -1388,13 +1388,20 @@ __device__ __forceinline__ int find_request(const ServeRequest* reqs, int nreq, 
   return lo;
 }
 
-// One warp (block) per pose, grid-stride over the tick's poses.
+// One warp (block) per pose, grid-stride over the tick's poses.  A pose index
+// that decodes outside its request (an inconsistent tick table) sets the
+// request's status word and is skipped.
 __global__ void __launch_bounds__(32) serve_setup_kernel(const ServeHeader* __restrict__ hdr,
-                                                         const ServeRequest* __restrict__ reqs) {
+                                                         const ServeRequest* __restrict__ reqs,
+                                                         unsigned int* __restrict__ status) {
   const int nreq = hdr->nreq, total = hdr->total_poses;
   for (int i = blockIdx.x; i < total; i += gridDim.x) {
     const int r = find_request(reqs, nreq, i, false);
     const int b = i - reqs[r].pose_start;
+    if (b < 0 || b >= reqs[r].B) {  // uniform in the warp
+      if (threadIdx.x == 0) atomicOr(status + r, kServePoseRange);
+      continue;
+    }
     warp_pose_geom(reqs[r].poses + 6 * b, reqs[r].det, reqs[r].vd, reqs[r].geom + b);
   }
 }
@@ -1417,6 +1424,7 @@ __device__ __forceinline__ void serve_trace(const VolumeDev& vd, const PoseGeom&
 // shared slots when they change.
 __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHeader* __restrict__ hdr,
                                                                  const ServeRequest* __restrict__ reqs,
+                                                                 unsigned int* __restrict__ status,
                                                                  int* __restrict__ counter) {
   __shared__ PoseGeom spg[kThreads / 32];
   __shared__ ServeRequest sreq[kThreads / 32];
@@ -1443,7 +1451,10 @@ __global__ void __launch_bounds__(kThreads, 4) serve_walk_kernel(const ServeHead
     const int per_pose = pose_tiles(sr.det);
     const int local = t - sr.tile_start;
     const int b = local / per_pose;
-    if (b < 0 || b >= sr.B) continue;  // the tick table's tile ranges, checked (uniform in the warp)
+    if (b < 0 || b >= sr.B) {  // the tick table's tile ranges, checked (uniform in the warp)
+      if (lane == 0) atomicOr(status + r, kServeTileRange);
+      continue;
+    }
     const int tin = local - b * per_pose;
     if (b != cur_b) {
       const unsigned int* src = reinterpret_cast<const unsigned int*>(sr.geom + b);
@@ -1500,6 +1511,7 @@ __global__ void __launch_bounds__(kFinThreads) serve_finalize_kernel(const Serve
     const ServeRequest& q = reqs[r];
     if (q.grad == nullptr) continue;  // uniform across the block
     const int b = i - q.pose_start;
+    if (b < 0 || b >= q.B) continue;  // flagged by serve_setup_kernel (same decode)
     const int nt = pose_tiles(q.det);
     sum_pose_partials(q.partials + static_cast<size_t>(b) * nt * 6, nt, 6, q.grad_pose + 6 * b);
   }
@@ -1721,15 +1733,15 @@ int serve_walk_grid(int device) {
   return max(1, sms * max(per_sm, 1));
 }
 
-cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, int* counter, int max_poses,
-                              int walk_grid, cudaStream_t stream) {
+cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, unsigned int* status, int* counter,
+                              int max_poses, int walk_grid, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
   // setup and finalize stride over the tick's poses: one block per pose up to
   // the walk's grid, so that a small tick does not pay for thousands of idle blocks
   const int aux = max(1, min(max_poses, walk_grid));
-  serve_setup_kernel<<<aux, 32, 0, stream>>>(hdr, reqs);
-  serve_walk_kernel<<<walk_grid, kThreads, 0, stream>>>(hdr, reqs, counter);
+  serve_setup_kernel<<<aux, 32, 0, stream>>>(hdr, reqs, status);
+  serve_walk_kernel<<<walk_grid, kThreads, 0, stream>>>(hdr, reqs, status, counter);
   serve_finalize_kernel<<<aux, kFinThreads, 0, stream>>>(hdr, reqs);
   return cudaGetLastError();
 }

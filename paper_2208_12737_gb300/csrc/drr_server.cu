@@ -65,6 +65,8 @@ struct Req {
   int64_t tick = -1;
   ReqState state = kPending;
   drr_status status = DRR_OK;
+  unsigned int device_status = 0;  // the tick's status word for this request, after the tick
+  unsigned int inject_status = 0;  // host-side fault injection: uploaded as the initial status word
 };
 
 struct Tick {
@@ -76,6 +78,27 @@ struct Tick {
   std::atomic<bool> done{false};
   struct drr_server_s* owner = nullptr;
 };
+
+// Layout of a tick's work: request i owns the tick's warp tiles
+// [tile_start[i], tile_start[i] + B_i * pose_tiles(det_i)) and poses
+// [pose_start[i], pose_start[i] + B_i), in admission order, back to back.  The
+// serving kernels decode a tile or pose index by a binary search over these
+// starts, so the ranges must be contiguous, ascending and cover every index
+// exactly once (tested on the CPU through drr_serve_tick_layout).
+bool layout_tick(int n, const int32_t* B, const drr::DetDev* det, int32_t* tile_start, int32_t* pose_start,
+                 int32_t* total_tiles, int32_t* total_poses) {
+  int64_t tiles = 0, poses = 0;
+  for (int i = 0; i < n; ++i) {
+    tile_start[i] = static_cast<int32_t>(tiles);
+    pose_start[i] = static_cast<int32_t>(poses);
+    tiles += int64_t(B[i]) * drr::pose_tiles(det[i]);  // the walk claims 8x4 warp tiles
+    poses += B[i];
+    if (tiles >= (int64_t{1} << 31) || poses >= (int64_t{1} << 31)) return false;
+  }
+  *total_tiles = static_cast<int32_t>(tiles);
+  *total_poses = static_cast<int32_t>(poses);
+  return true;
+}
 
 // Sizes of a request's device and staging buffers (each piece 256-B aligned).
 void size_request(Req& q) {
@@ -102,13 +125,15 @@ struct drr_server_s {
   drr::OffsetArena* dev_arena = nullptr;
   drr::OffsetArena* host_arena = nullptr;
   struct Set {
-    char* h_table = nullptr;  // pinned: header + requests
+    char* h_table = nullptr;  // pinned: header + requests + per-request status words
     char* d_table = nullptr;
     int* d_counter = nullptr;
     cudaGraphExec_t graph = nullptr;
   } sets[2];
   size_t table_bytes = 0;
+  size_t status_off = 0;  // offset of the status words in a table
   int walk_grid = 1;
+  int waiters = 0;  // threads inside drr_server_wait (destroy waits for them to leave)
 
   std::mutex mu;
   std::condition_variable cv_loop, cv_done;
@@ -152,7 +177,8 @@ cudaError_t drr_server_s::launch_kernels(int set) {
   if (st.graph) return cudaGraphLaunch(st.graph, stream);
   const auto* hdr = reinterpret_cast<const drr::ServeHeader*>(st.d_table);
   const auto* rq = reinterpret_cast<const drr::ServeRequest*>(st.d_table + sizeof(drr::ServeHeader));
-  return drr::launch_serve_tick(hdr, rq, st.d_counter, cfg.max_tick_poses, walk_grid, stream);
+  auto* status = reinterpret_cast<unsigned int*>(st.d_table + status_off);
+  return drr::launch_serve_tick(hdr, rq, status, st.d_counter, cfg.max_tick_poses, walk_grid, stream);
 }
 
 // Admit requests (FIFO) into a new tick and enqueue it.  Called with lk held;
@@ -207,7 +233,20 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   Set& st = sets[t->set];
   auto* hdr = reinterpret_cast<drr::ServeHeader*>(st.h_table);
   auto* rq = reinterpret_cast<drr::ServeRequest*>(st.h_table + sizeof(drr::ServeHeader));
-  int tile_start = 0, pose_start = 0;
+  const int n = static_cast<int>(batch.size());
+  std::vector<int32_t> Bs(n), tstart(n), pstart(n);
+  std::vector<drr::DetDev> dets(n);
+  for (int i = 0; i < n; ++i) {
+    Bs[i] = batch[i]->r.B;
+    dets[i] = batch[i]->det;
+  }
+  int32_t total_tiles = 0, total_poses = 0;
+  // admission caps the tick at max_tick_poses <= 2^20 poses of < 2^30 tiles each
+  // request, so the layout always fits; a failure leaves the tick empty
+  if (!layout_tick(n, Bs.data(), dets.data(), tstart.data(), pstart.data(), &total_tiles, &total_poses)) {
+    total_tiles = total_poses = 0;
+    if (e == cudaSuccess) e = cudaErrorInvalidValue;
+  }
   for (size_t i = 0; i < batch.size(); ++i) {
     Req* q = batch[i];
     q->tick = t->id;
@@ -240,21 +279,24 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     sr.grad_pose = q->d_gpose;
     sr.geom = q->d_geom;
     sr.B = q->r.B;
-    sr.tile_start = tile_start;
-    sr.pose_start = pose_start;
-    tile_start += static_cast<int>(B * nt);  // the walk claims 8x4 warp tiles
-    pose_start += static_cast<int>(B);
+    sr.tile_start = tstart[i];
+    sr.pose_start = pstart[i];
   }
   hdr->nreq = static_cast<int>(batch.size());
-  hdr->total_tiles = tile_start;
-  hdr->total_poses = pose_start;
+  hdr->total_tiles = total_tiles;
+  hdr->total_poses = total_poses;
   hdr->pad_ = 0;
+  auto* h_status = reinterpret_cast<unsigned int*>(st.h_table + status_off);
+  for (size_t i = 0; i < batch.size(); ++i) h_status[i] = batch[i]->inject_status;  // normally 0
   const size_t tbytes = sizeof(drr::ServeHeader) + batch.size() * sizeof(drr::ServeRequest);
+  const size_t sbytes = batch.size() * sizeof(unsigned int);
   // The table set and the request buffers written here belong to no tick still
   // in flight: this tick's set was last used two ticks ago, which has finished
   // (its result copies, after its kernels, are done), and the arenas hand out
   // only memory of finished ticks.
   if (e == cudaSuccess) e = cudaMemcpyAsync(st.d_table, st.h_table, tbytes, cudaMemcpyHostToDevice, h2d);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(st.d_table + status_off, h_status, sbytes, cudaMemcpyHostToDevice, h2d);
   for (Req* q : batch) {
     if (e != cudaSuccess) break;
     e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->r.B) * 6 * 4, cudaMemcpyHostToDevice, h2d);
@@ -268,6 +310,8 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   if (e == cudaSuccess) drr::count_launches(3);
   if (e == cudaSuccess) e = cudaEventRecord(t->stop, stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, t->stop, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h_status, st.d_table + status_off, sbytes, cudaMemcpyDeviceToHost, d2h);
   for (Req* q : batch) {
     if (e != cudaSuccess) break;
     e = cudaMemcpyAsync(q->h_out, q->d_out, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, d2h);
@@ -299,8 +343,15 @@ void drr_server_s::sync_streams() {
 // tick is off the in-flight list and its requests are admitted (not done), so
 // no other thread touches them or their callers' buffers meanwhile.
 void drr_server_s::copy_results(Tick* t) {
-  for (Req* q : t->reqs) {
+  const auto* h_status = reinterpret_cast<const unsigned int*>(sets[t->set].h_table + status_off);
+  for (size_t i = 0; i < t->reqs.size(); ++i) {
+    Req* q = t->reqs[i];
     if (q->status != DRR_OK) continue;
+    q->device_status = h_status[i];
+    if (q->device_status != 0) {  // a kernel flagged this request: its outputs are not trusted
+      q->status = DRR_ERR_DEVICE;
+      continue;
+    }
     std::memcpy(q->r.drr_out, q->h_out, size_t(q->r.B) * q->npix * 4);
     if (q->grad) std::memcpy(q->r.grad_pose_out, q->h_gpose, size_t(q->r.B) * 6 * 4);
   }
@@ -381,7 +432,8 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_base), cfg.device_budget_bytes);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_base), cfg.host_budget_bytes, 0);
-  s->table_bytes = sizeof(drr::ServeHeader) + size_t(cfg.max_inflight) * sizeof(drr::ServeRequest);
+  s->status_off = up(sizeof(drr::ServeHeader) + size_t(cfg.max_inflight) * sizeof(drr::ServeRequest));
+  s->table_bytes = s->status_off + size_t(cfg.max_inflight) * sizeof(unsigned int);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaHostAlloc(reinterpret_cast<void**>(&s->sets[i].h_table), s->table_bytes, 0);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->sets[i].d_table), s->table_bytes);
@@ -479,12 +531,17 @@ drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, dr
   if (it == s->reqs.end()) return drr::set_error(DRR_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
   Req* q = it->second;
   auto ready = [q] { return q->state == kDone; };
+  ++s->waiters;  // drr_server_destroy frees nothing while a waiter is inside
+  bool finished = true;
   if (timeout_ms < 0) {
     s->cv_done.wait(lk, ready);
-  } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+  } else {
+    finished = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  }
+  if (--s->waiters == 0) s->cv_done.notify_all();
+  if (!finished)
     return drr::set_error(DRR_ERR_TIMEOUT, "ticket %llu not finished after %d ms", (unsigned long long)ticket,
                           timeout_ms);
-  }
   if (res) {
     res->status = q->status;
     res->queue_ms = q->tick >= 0 ? ms_between(q->t_submit, q->t_admit) : 0.0;
@@ -492,9 +549,33 @@ drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, dr
     res->tick = q->tick;
   }
   drr_status st = q->status;
+  const unsigned int dev_bits = q->device_status;
   s->reqs.erase(it);
   delete q;
+  if (st == DRR_ERR_DEVICE)
+    return drr::set_error(st, "request %llu: a serving kernel set its status word (bits 0x%x); outputs not written",
+                          (unsigned long long)ticket, dev_bits);
   if (st != DRR_OK) return drr::set_error(st, "request %llu did not complete", (unsigned long long)ticket);
+  return DRR_OK;
+}
+
+drr_status drr_server_poll(drr_server s, uint64_t ticket, int32_t* state) {
+  if (!s || !state) return drr::set_error(DRR_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return drr::set_error(DRR_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  const Req* q = it->second;
+  *state = q->state == kPending ? DRR_REQ_QUEUED : (q->state == kAdmitted ? DRR_REQ_RUNNING : DRR_REQ_DONE);
+  return DRR_OK;
+}
+
+drr_status drr_server_inject_device_status(drr_server s, uint64_t ticket, uint32_t bits) {
+  if (!s) return drr::set_error(DRR_ERR_INVALID, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return drr::set_error(DRR_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  if (it->second->state != kPending) return drr::set_error(DRR_ERR_BUSY, "request already admitted");
+  it->second->inject_status = bits;
   return DRR_OK;
 }
 
@@ -574,6 +655,13 @@ drr_status drr_server_destroy(drr_server s) {
   s->cv_done.notify_all();
   if (s->loop.joinable()) s->loop.join();
   s->sync_streams();
+  {
+    // every request is done now; threads still inside drr_server_wait return
+    // once they reacquire the lock, and nothing is freed before they have left
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.notify_all();
+    s->cv_done.wait(lk, [s] { return s->waiters == 0; });
+  }
   for (auto& kv : s->reqs) delete kv.second;
   s->reqs.clear();
   for (auto& st : s->sets) {
@@ -590,6 +678,20 @@ drr_status drr_server_destroy(drr_server s) {
   delete s->dev_arena;
   delete s->host_arena;
   delete s;
+  return DRR_OK;
+}
+
+drr_status drr_serve_tick_layout(int32_t n, const int32_t* B, const drr_detector* dets, int32_t* tile_start,
+                                 int32_t* pose_start, int32_t* totals) {
+  if (n <= 0 || !B || !dets || !tile_start || !pose_start || !totals)
+    return drr::set_error(DRR_ERR_INVALID, "bad arguments");
+  std::vector<drr::DetDev> dd(n);
+  for (int i = 0; i < n; ++i) {
+    if (drr_status s = drr::check_detector(&dets[i], &dd[i])) return s;
+    if (B[i] <= 0) return drr::set_error(DRR_ERR_INVALID, "B must be positive");
+  }
+  if (!layout_tick(n, B, dd.data(), tile_start, pose_start, &totals[0], &totals[1]))
+    return drr::set_error(DRR_ERR_INVALID, "tick too large");
   return DRR_OK;
 }
 

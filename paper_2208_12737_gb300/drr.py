@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdrr.so")
 
 DRR_F32, DRR_BF16, DRR_F16, DRR_I16_HU = 0, 1, 2, 3
+LAYOUT = {"default": 0, "x": 1, "y": 2, "z": 3}  # drr_layout: the fastest axis of the padded storage
 _STATUS = {0: "DRR_OK", 1: "DRR_ERR_INVALID", 2: "DRR_ERR_OOM", 3: "DRR_ERR_CUDA", 4: "DRR_ERR_TIMEOUT",
            5: "DRR_ERR_BUSY", 6: "DRR_ERR_NOT_FOUND", 7: "DRR_ERR_DEVICE", 8: "DRR_ERR_CANCELLED"}
 STORAGE = {"f32": DRR_F32, "bf16": DRR_BF16, "f16": DRR_F16}
@@ -30,6 +31,7 @@ EXPORTS = (
     "drr_server_pause", "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
     "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc", "drr_zncc", "drr_adam_step",
     "drr_loss_landscape", "drr_geometry_grad", "drr_probe_l2_read", "drr_render_plain_fp32",
+    "drr_server_poll", "drr_server_inject_device_status", "drr_serve_tick_layout",
 )
 
 
@@ -117,6 +119,9 @@ def load(path: str = LIB_PATH):
         lib.drr_server_get_stats.argtypes = [_vp, ctypes.POINTER(drr_server_stats)]
         lib.drr_server_destroy.argtypes = [_vp]
         lib.drr_server_pause.argtypes = [_vp, _i32]
+        lib.drr_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(_i32)]
+        lib.drr_server_inject_device_status.argtypes = [_vp, ctypes.c_uint64, ctypes.c_uint32]
+        lib.drr_serve_tick_layout.argtypes = [_i32, _vp, _vp, _vp, _vp, _vp]
         lib.drr_arena_create.argtypes = [ctypes.c_size_t, ctypes.c_size_t, ctypes.POINTER(_vp)]
         lib.drr_arena_alloc.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
         lib.drr_arena_free.argtypes = [_vp, ctypes.c_size_t]
@@ -186,7 +191,7 @@ class Volume:
     """
 
     def __init__(self, data, spacing, storage: str = "f32", hu: bool = False, mu_water: float = 0.02,
-                 layout: int = 0, stream=None):
+                 layout="default", stream=None):
         import torch
         lib = load()
         self._lib = lib
@@ -211,7 +216,8 @@ class Volume:
         if len(shape) != 3:
             raise ValueError("volume must be (nz, ny, nx)")
         nz, ny, nx = shape
-        opt = drr_volume_options(STORAGE[storage], float(mu_water) if hu else 0.0, int(layout), (0, 0, 0))
+        lay = LAYOUT[layout] if isinstance(layout, str) else int(layout)
+        opt = drr_volume_options(STORAGE[storage], float(mu_water) if hu else 0.0, lay, (0, 0, 0))
         torch.cuda.init()
         check(lib.drr_volume_create(ptr, on_dev, src_dtype, nx, ny, nz, float(spacing[0]), float(spacing[1]),
                                     float(spacing[2]), ctypes.byref(opt), _stream_ptr(stream),
@@ -492,6 +498,17 @@ class Ticket:
 
     def cancel(self):
         check(self.server._lib.drr_server_cancel(self.server.h, self.id))
+
+    def poll(self) -> str:
+        """'queued', 'running' or 'done', without waiting (the ticket is kept)."""
+        st = _i32()
+        check(self.server._lib.drr_server_poll(self.server.h, self.id, ctypes.byref(st)))
+        return ("queued", "running", "done")[st.value]
+
+    def inject_device_status(self, bits: int):
+        """Test hook: make this queued request's device status word start with `bits`
+        set, so the server reports DRR_ERR_DEVICE for it after its tick."""
+        check(self.server._lib.drr_server_inject_device_status(self.server.h, self.id, int(bits)))
 
 
 class Server:

@@ -201,3 +201,89 @@ def test_backlog_is_split_between_two_ticks(drr, vols):
     for i in (0, 17, 39):
         np.testing.assert_array_equal(outs[i], _direct(drr, vol, det, poses[i])[0])
     srv.close()
+
+
+def test_device_status_word_fails_only_its_request(drr, vols):
+    # The status path end to end without a bad table: the host uploads one
+    # request's status word with a bit already set, the kernels leave it, the
+    # word comes back with the tick's results, and that request (only) ends
+    # with DRR_ERR_DEVICE; a clean mix leaves every word at zero (all other
+    # serving tests complete with DRR_OK).
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 20, 24, 1.5, 1.5)
+    srv = drr.Server(device_budget=64 << 20)
+    srv.pause(True)
+    poses = [inputs.random_poses(1, seed=400 + i) for i in range(5)]
+    g = inputs.upstream_grad((1, 20, 24), seed=401)
+    tickets = [srv.submit(vol, det, p, g if i % 2 else None) for i, p in enumerate(poses)]
+    tickets[2].inject_device_status(1)
+    assert [t.poll() for t in tickets] == ["queued"] * 5
+    srv.pause(False)
+    for i, t in enumerate(tickets):
+        if i == 2:
+            with pytest.raises(drr.DrrError) as ei:
+                t.wait(20000)
+            assert ei.value.status == 7  # DRR_ERR_DEVICE
+            assert "status word" in str(ei.value)
+        else:
+            E, G = t.wait(20000)
+            E_d, G_d = _direct(drr, vol, det, poses[i], g if i % 2 else None)
+            np.testing.assert_array_equal(E, E_d)
+            if i % 2:
+                np.testing.assert_array_equal(G, G_d)
+    st = srv.stats()
+    assert st["failed"] == 1 and st["completed"] == 4
+    # admitted requests can no longer be flagged from the host
+    t = srv.submit(vol, det, poses[0])
+    t.wait(20000)
+    with pytest.raises(drr.DrrError) as ei:
+        t.poll()
+    assert ei.value.status == 6  # released by wait
+    srv.close()
+
+
+def test_poll_reports_queued_running_done(drr, vols):
+    data, sp, vol = vols["hu"]
+    det = inputs.Detector(300.0, 64, 64, 1.5, 1.5)
+    srv = drr.Server(device_budget=64 << 20)
+    srv.pause(True)
+    t = srv.submit(vol, det, inputs.random_poses(2, seed=410))
+    assert t.poll() == "queued"
+    srv.pause(False)
+    import time
+    deadline = time.time() + 20
+    while t.poll() != "done" and time.time() < deadline:
+        time.sleep(0.001)
+    assert t.poll() == "done"
+    t.wait(0)
+    srv.close()
+
+
+def test_destroy_while_threads_wait(drr, vols):
+    # drr_server_destroy returns only after threads blocked in drr_server_wait
+    # have left it: each waiter gets its request's result or a cancellation
+    import threading
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 48, 48, 1.5, 1.5)
+    srv = drr.Server(device_budget=64 << 20)
+    srv.pause(True)
+    tickets = [srv.submit(vol, det, inputs.random_poses(1, seed=420 + i)) for i in range(6)]
+    codes = []
+
+    def waiter(t):
+        try:
+            t.wait(-1)
+            codes.append(0)
+        except drr.DrrError as e:
+            codes.append(e.status)
+
+    threads = [threading.Thread(target=waiter, args=(t,)) for t in tickets]
+    for th in threads:
+        th.start()
+    import time
+    time.sleep(0.2)
+    srv.close()
+    for th in threads:
+        th.join(timeout=30)
+        assert not th.is_alive()
+    assert sorted(codes) == [8] * 6  # all were queued (paused): cancelled
