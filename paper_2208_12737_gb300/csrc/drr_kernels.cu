@@ -963,74 +963,109 @@ __device__ __forceinline__ void geometry_jacobian(const RaySetup& r, const JacSu
 }
 
 // Back-projection adds of one warp step, merged down each column of the warp's
-// TW x (32 / TW) pixel tile: the lanes of one column (pixels h, h+1, ... at the same w)
-// whose rays are in the same voxel at this step add once, through the first
-// lane of each run of equal addresses, the run's sum found by a segmented
+// TW x (32 / TW) pixel tile: the lanes of one column (pixels h, h+1, ... at the
+// same w) whose rays are in the same voxel at this step add once, through the
+// first lane of each run of equal addresses, the run's sum found by a segmented
 // suffix scan over the column.  The L2 serves every lane's atomic as its own
 // sector operation, so each lane merged away is one L2 operation less; rays a
 // pixel apart along h often share a voxel (2.5 mm CT slices against 0.7 mm
 // pixels at the isocentre).  Addresses at or beyond nvox add nothing.
+#ifndef DRR_BP_MERGE_ROWS
+#define DRR_BP_MERGE_ROWS 8  // runs are merged within aligned groups of this many rows (a power of two)
+#endif
 template <int TW>
 __device__ __forceinline__ void red_column_merged(float* __restrict__ gvol, unsigned int addr, float v,
                                                   unsigned int nvox, int lane) {
   constexpr unsigned int kAll = 0xffffffffu;
   constexpr int TH = 32 / TW;
+  constexpr int kRows = DRR_BP_MERGE_ROWS < TH ? DRR_BP_MERGE_ROWS : TH;
   const int hrow = lane / TW;
   const unsigned int a_dn = __shfl_down_sync(kAll, addr, TW);
-  bool lk = hrow < TH - 1 && a_dn == addr;  // the pixel below adds to the same voxel
+  bool lk = (hrow + 1) % kRows != 0 && a_dn == addr;  // the pixel below adds to the same voxel
   const unsigned int first = __ballot_sync(kAll, lk);
   unsigned int lkm = first;
   float s = v;
 #pragma unroll
-  for (int d = 1; d < TH; d *= 2) {
+  for (int d = 1; d < kRows; d *= 2) {
     // s: the run's sum over rows hrow .. hrow + d - 1; lk: the run goes on past them
     const float s_dn = __shfl_down_sync(kAll, s, d * TW);
     if (lk) s += s_dn;
-    if (2 * d < TH) {
+    if (2 * d < kRows) {
       lk = lk && ((lkm >> ((lane + d * TW) & 31)) & 1u);
       lkm = __ballot_sync(kAll, lk);
     }
   }
-  const bool head = hrow == 0 || !((first >> ((lane - TW) & 31)) & 1u);
+  // the first row of each run within its group adds
+  const bool head = hrow % kRows == 0 || !((first >> ((lane - TW) & 31)) & 1u);
   if (head && addr < nvox) atomicAdd(gvol + addr, s);
 }
 
 // Back-projection walk: grad_V[voxel] += g L (a_{m+1} - a_m), the transpose of
-// the forward map V -> E; into an unpadded (nz, ny, nx) FP32 volume.  Segment
-// lengths are exact integers in units of span / 2^29 (bits 27..58 of the fixed
-// point).  Called by all 32 lanes of the warp together (the adds are merged
-// across lanes); a lane whose pixel has no ray to walk passes nseg = 0 and
-// adds nothing.
+// the forward map V -> E (Eq. 2 is linear in V), into an unpadded (nz, ny, nx)
+// FP32 volume.  The crossings are those of the forward walk: FP32 positions
+// local to an exact fixed-point anchor, re-anchored every kBpChunk steps.  All
+// 32 lanes step together (to the warp's longest ray) and re-anchor at the same
+// steps, since their adds are merged across lanes; a lane whose pixel has no
+// ray to walk passes nseg = 0 and adds nothing.
+constexpr int kBpChunk = 64;
 __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RaySetup& r, int nseg, float gL,
-                                                 float* __restrict__ gvol, int lane) {
-  unsigned long long Ax = r.A0[0], Ay = r.A0[1], Az = r.A0[2];
+                                                 float* __restrict__ gvol, WalkScratch* ws, int lane) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ws->A0[a][t] = r.A0[a];
+    ws->D[a][t] = r.D[a];
+  }
+  const float dx = fix_to_float(static_cast<long long>(r.D[0])), dy = fix_to_float(static_cast<long long>(r.D[1])),
+              dz = fix_to_float(static_cast<long long>(r.D[2]));
   // unsigned index arithmetic: a lane past its exit keeps stepping (wrapping) without adding
   const unsigned int nx = static_cast<unsigned int>(vd.n[0]), nxy = nx * static_cast<unsigned int>(vd.n[1]);
-  const unsigned int lx = r.step[0] > 0 ? 1u : 0u - 1u;
-  const unsigned int ly = r.step[1] > 0 ? nx : 0u - nx;
-  const unsigned int lz = r.step[2] > 0 ? nxy : 0u - nxy;
+  const unsigned int sx = r.step[0] > 0 ? 1u : 0u - 1u;
+  const unsigned int sy = r.step[1] > 0 ? nx : 0u - nx;
+  const unsigned int sz = r.step[2] > 0 ? nxy : 0u - nxy;
   const unsigned int nvox = static_cast<unsigned int>(vd.n[0] * vd.n[1] * vd.n[2]);
   unsigned int lin = static_cast<unsigned int>(r.ient[0] + vd.n[0] * (r.ient[1] + vd.n[1] * r.ient[2]));
-  constexpr int kShift = 27;
-  constexpr unsigned int kExit = kExitUnits << (32 - kShift);  // 2^29
-  const float s = gL * r.unit * (1.f / static_cast<float>(1u << (32 - kShift)));
+  const float s = gL * r.unit;  // gradient per high-word unit of segment length
   const int nmax = __reduce_max_sync(0xffffffffu, nseg);
-  unsigned int ac = 0u;
-  for (int m = 1; m <= nmax; ++m) {  // step m adds segment m - 1; step nseg adds the exit segment
-    const unsigned int hx = static_cast<unsigned int>(Ax >> kShift), hy = static_cast<unsigned int>(Ay >> kShift),
-                       hz = static_cast<unsigned int>(Az >> kShift);
-    const unsigned int an = min(min(hx, hy), hz);
-    const unsigned int to = m < nseg ? an : kExit;
-    const float v = s * static_cast<float>(static_cast<int>(to - ac));
-    red_column_merged<kBpTileW>(gvol, m <= nseg ? lin : 0xffffffffu, v, nvox, lane);
-    ac = an;
-    const bool bx = hx == an;
-    const bool by = !bx && hy == an;
-    const bool bz = !bx && !by;
-    lin += bx ? lx : (by ? ly : lz);
-    if (bx) Ax += r.D[0];
-    if (by) Ay += r.D[1];
-    if (bz) Az += r.D[2];
+  unsigned int kx = 0u, ky = 0u, kz = 0u;
+  unsigned long long O = 0ull;  // exact position of the last crossing taken (the anchor)
+  float ac = 0.f;               // local position where the current segment starts
+  for (int m = 0; m < nmax;) {  // warp-uniform
+    const int n = min(nmax - m, kBpChunk);
+    const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], kx), O);
+    const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], ky), O);
+    const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], kz), O);
+    const float xe = local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O);
+    float tx = x0, ty = y0, tz = z0;
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+#pragma unroll 4
+    for (int j = 1; j <= n; ++j) {
+      const int step = m + j;  // this step ends segment step - 1 (the exit segment at step nseg)
+      const float an = fminf(fminf(tx, ty), tz);
+      const float val = s * ((step < nseg ? an : xe) - ac);
+      red_column_merged<kBpTileW>(gvol, step <= nseg ? lin : 0xffffffffu, val, nvox, lane);
+      ac = an;
+      const bool bx = tx == an;
+      const bool by = !bx && ty == an;
+      const bool bz = !bx && !by;
+      lin += bx ? sx : (by ? sy : sz);
+      if (bx) cx += 1.f;
+      if (by) cy += 1.f;
+      if (bz) cz += 1.f;
+      next_xy(tx, ty, cx, cy, dx, dy, x0, y0);
+      tz = fmaf(cz, dz, z0);
+    }
+    m += n;
+    kx += static_cast<unsigned int>(cx);
+    ky += static_cast<unsigned int>(cy);
+    kz += static_cast<unsigned int>(cz);
+    // re-anchor at the last crossing taken: the current segment starts there
+    unsigned long long Onew = O;
+    if (kx) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], kx - 1u));
+    if (ky) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], ky - 1u));
+    if (kz) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], kz - 1u));
+    ac = 0.f;
+    O = Onew;
   }
 }
 
@@ -1038,7 +1073,7 @@ __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RayS
 // with nseg = 0 where its pixel is outside the detector, its upstream gradient
 // is zero, the ray misses the volume or the geometry is not finite.
 __device__ __forceinline__ void backproject_tile_ray(const VolumeDev& vd, const PoseGeom& pg, int h, int w, bool active,
-                                                     float g, float* __restrict__ gvol, int lane) {
+                                                     float g, float* __restrict__ gvol, WalkScratch* ws, int lane) {
   RaySetup r{};
   int nseg = 0;
   float gL = 0.f;
@@ -1046,7 +1081,7 @@ __device__ __forceinline__ void backproject_tile_ray(const VolumeDev& vd, const 
     nseg = r.nseg;
     gL = g * sqrtf(fmaf(r.d[2], r.d[2], fmaf(r.d[1], r.d[1], r.d[0] * r.d[0])));
   }
-  walk_backproject(vd, r, nseg, gL, gvol, lane);
+  walk_backproject(vd, r, nseg, gL, gvol, ws, lane);
 }
 
 template <int MODE>
@@ -1126,7 +1161,8 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
   grid_dep_wait();
   grid_dep_release();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int TW = MODE == kBackproject ? kBpTileW : kWarpTileW, TH = 32 / TW;
+  constexpr bool kBp = MODE == kBackproject;
+  constexpr int TW = kBp ? kBpTileW : kWarpTileW, TH = 32 / TW;
   const int twx = (det.W + TW - 1) / TW;
   const int per_pose = twx * ((det.H + TH - 1) / TH);
   const unsigned int total = static_cast<unsigned int>(per_pose) * static_cast<unsigned int>(B);
@@ -1154,9 +1190,9 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
     RayResult r;
     r.nseg = 0;
     float gsc = 0.f;
-    if (valid && (MODE == kPoseGrad || MODE == kGeoGrad || MODE == kBackproject)) gsc = gin[b * npix + pix];
-    if (MODE == kBackproject) {
-      backproject_tile_ray(vd, pg, h, w, valid && gsc != 0.f, gsc, gvol, lane);
+    if (valid && (MODE == kPoseGrad || MODE == kGeoGrad || kBp)) gsc = gin[b * npix + pix];
+    if (kBp) {
+      backproject_tile_ray(vd, pg, h, w, valid && gsc != 0.f, gsc, gvol, &ws, lane);
       continue;
     }
     if (valid) {

@@ -205,6 +205,27 @@ def test_backprojection_vs_oracle(drr):
     np.testing.assert_allclose(gv.cpu().numpy(), ref, atol=2e-5 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+def test_backprojection_odd_volume_and_alignment(drr, offset):
+    # an odd voxel count, the last voxel reached, and a gradient volume 8-byte or
+    # only 4-byte aligned: nothing is added outside it
+    rng = np.random.default_rng(69)
+    shape, sp = (7, 9, 11), (0.9, 1.1, 1.2)
+    det = inputs.Detector(50.0, 13, 11, 1.2, 1.3)
+    poses_np = inputs.random_poses(2, seed=79, max_angle_deg=40)  # reaches the last voxel
+    g_np = inputs.upstream_grad((2, 13, 11), seed=71)
+    vol = drr.Volume(rng.uniform(0, 1, shape).astype(np.float32), sp)
+    n = int(np.prod(shape))
+    buf = torch.zeros(n + 1, device="cuda", dtype=torch.float32)
+    gv = buf[offset:offset + n].view(shape)
+    drr.render_backward(vol, det, torch.from_numpy(poses_np).cuda(), torch.from_numpy(g_np).cuda(), pose_grad=False,
+                        grad_volume=gv)
+    ref = oracle.backproject(shape, osp(sp), odet(det), poses_np, g_np.astype(np.float64))
+    np.testing.assert_allclose(gv.cpu().numpy(), ref, atol=2e-5 * np.abs(ref).max())
+    assert float(buf[n if offset == 0 else 0]) == 0.0  # nothing added outside the volume
+    assert ref.reshape(-1)[-1] != 0  # the odd last voxel is reached
+
+
 def test_backprojection_with_shared_voxels_and_gaps(drr):
     # Thick slices along z, so that rays a pixel apart along h cross the same
     # voxels and the warp merges their adds; zero upstream gradients and rays
