@@ -79,10 +79,11 @@ typedef struct {
  * linear storage (one zero voxel of padding on each face, so every gather of
  * the walk is in bounds): a voxel step along any axis moves the walk's offset
  * by one fixed signed stride.  They differ in which axis is fastest, i.e. in
- * which neighbouring voxels share a cache sector.  The best choice puts the
- * axis along which a warp's rays (an 8 x 4 pixel tile, detector columns first)
- * are spread fastest: for the canonical pose, whose detector columns run
- * along y, that is DRR_LAYOUT_LINEAR_Y. */
+ * which neighbouring voxels share a cache line.  A ray reuses a line for as
+ * long as it moves along the fastest axis, so the best choice is the axis the
+ * rays mostly run along: x for poses near the canonical one (source on +x).
+ * On the 16-pose CT batch (rays within 45 degrees of x) the fwd+Jacobian walk
+ * takes 0.567 / 0.583 / 0.643 ms with x / y / z fastest (same bits). */
 typedef enum {
   DRR_LAYOUT_DEFAULT = 0,  /* = DRR_LAYOUT_LINEAR_X */
   DRR_LAYOUT_LINEAR_X = 1, /* x fastest, then y, then z */
@@ -95,8 +96,11 @@ typedef struct {
   drr_dtype storage;  /* DRR_F32 (default), DRR_BF16 or DRR_F16 */
   float hu_mu_water;  /* attenuation of water in /mm for DRR_I16_HU input:
                          mu = max(0, mu_water (1 + HU/1000)); 0 -> 0.02 */
-  int32_t layout;     /* a drr_layout; other values are DRR_ERR_INVALID */
-  int32_t brick[3];   /* reserved, must be zero */
+  int32_t layout;     /* a drr_layout; other values are DRR_ERR_INVALID.  (A
+                         bricked layout, 8 x 4 x 1 voxels per 128-byte line, was
+                         measured slower than DRR_LAYOUT_LINEAR_X: 0.471 against
+                         0.370 ms for the 16-pose CT forward batch; it is not
+                         offered.) */
 } drr_volume_options;
 
 /* ---- volumes (Sec. 2.2: the CT volume V and its spacing) ---------------- */

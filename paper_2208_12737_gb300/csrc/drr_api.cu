@@ -264,8 +264,6 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
     if (opt->layout < 0 || opt->layout > DRR_LAYOUT_LINEAR_Z)
       return drr::set_error(DRR_ERR_INVALID, "layout %d not supported (0 .. 3)", opt->layout);
     if (opt->layout != 0) layout = opt->layout;
-    if (opt->brick[0] != 0 || opt->brick[1] != 0 || opt->brick[2] != 0)
-      return drr::set_error(DRR_ERR_INVALID, "brick must be zero: the layouts are padded linear");
   }
   if (storage != DRR_F32 && storage != DRR_BF16 && storage != DRR_F16)
     return drr::set_error(DRR_ERR_INVALID, "storage dtype must be DRR_F32, DRR_BF16 or DRR_F16");

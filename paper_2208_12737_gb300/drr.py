@@ -47,8 +47,7 @@ class drr_detector(ctypes.Structure):
 
 
 class drr_volume_options(ctypes.Structure):
-    _fields_ = [("storage", ctypes.c_int32), ("hu_mu_water", ctypes.c_float), ("layout", ctypes.c_int32),
-                ("brick", ctypes.c_int32 * 3)]
+    _fields_ = [("storage", ctypes.c_int32), ("hu_mu_water", ctypes.c_float), ("layout", ctypes.c_int32)]
 
 
 class drr_server_config(ctypes.Structure):
@@ -217,7 +216,7 @@ class Volume:
             raise ValueError("volume must be (nz, ny, nx)")
         nz, ny, nx = shape
         lay = LAYOUT[layout] if isinstance(layout, str) else int(layout)
-        opt = drr_volume_options(STORAGE[storage], float(mu_water) if hu else 0.0, lay, (0, 0, 0))
+        opt = drr_volume_options(STORAGE[storage], float(mu_water) if hu else 0.0, lay)
         torch.cuda.init()
         check(lib.drr_volume_create(ptr, on_dev, src_dtype, nx, ny, nz, float(spacing[0]), float(spacing[1]),
                                     float(spacing[2]), ctypes.byref(opt), _stream_ptr(stream),

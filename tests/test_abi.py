@@ -91,15 +91,13 @@ def test_volume_limits_are_checked_before_any_device_work(lib):
 
 def test_only_the_padded_linear_layouts_and_known_storage_are_accepted(lib):
     class Options(ctypes.Structure):  # drr_volume_options of include/drr.h
-        _fields_ = [("storage", ctypes.c_int32), ("hu_mu_water", ctypes.c_float), ("layout", ctypes.c_int32),
-                    ("brick", ctypes.c_int32 * 3)]
+        _fields_ = [("storage", ctypes.c_int32), ("hu_mu_water", ctypes.c_float), ("layout", ctypes.c_int32)]
     buf = ctypes.create_string_buffer(4 * 64)
     out = ctypes.c_void_p()
     lib.drr_volume_create.restype = ctypes.c_int
     lib.drr_last_error.restype = ctypes.c_char_p
-    for opt, word in ((Options(0, 0.0, 4, (0, 0, 0)), b"layout"), (Options(0, 0.0, -1, (0, 0, 0)), b"layout"),
-                      (Options(0, 0.0, 2, (4, 4, 4)), b"brick"), (Options(3, 0.0, 0, (0, 0, 0)), b"storage"),
-                      (Options(0, -1.0, 0, (0, 0, 0)), b"mu_water")):
+    for opt, word in ((Options(0, 0.0, 4), b"layout"), (Options(0, 0.0, -1), b"layout"),
+                      (Options(3, 0.0, 0), b"storage"), (Options(0, -1.0, 0), b"mu_water")):
         st = lib.drr_volume_create(buf, 0, 0, 4, 4, 4, ctypes.c_float(1.0), ctypes.c_float(1.0), ctypes.c_float(1.0),
                                    ctypes.byref(opt), None, ctypes.byref(out))
         assert st == 1 and word in lib.drr_last_error() and out.value is None
