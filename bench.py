@@ -305,81 +305,16 @@ def serving_volumes(drr, hu133):
     return vols
 
 
-def fifo_latencies(arrivals, service):
-    """Latency of each request (s) at a single server taking them in arrival order."""
-    t_free, lat = 0.0, []
-    for at, s_ in zip(arrivals, service):
-        t_free = max(at, t_free) + s_
-        lat.append(t_free - at)
-    return np.array(lat)
+SERVE_TICK_WORK = 1 << 30  # ray-planes admitted into one tick (about 0.5-0.8 ms of walk)
 
 
-def plain_fifo_server(drr, reqs, arrivals, h_rot=1e-3, h_trans=1e-2):
-    """The same requests at the same arrival times, served one at a time in arrival
-    order by the plain FP32 forward walk, a gradient request by central differences
-    on it (13 renders in one call): each request's device time (pose upload, renders,
-    the difference sums, DRR and gradient download) is measured on the GPU, and the
-    queue is then replayed from those times."""
-    import torch
-    svc = []
-    step = np.array([h_rot] * 3 + [h_trans] * 3)
-    # untimed warm-up on every resident volume at the largest detector (first
-    # kernel loads per storage type, first torch ops, the largest allocations)
-    from paper_2208_12737_gb300 import inputs
-    seen = {}
-    for v, _, pose, _ in reqs:
-        seen.setdefault(id(v), (v, pose))
-    big = inputs.Detector(510.0, 512, 512, 280.0 / 512, 280.0 / 512)
-    g_big = torch.ones((1, 512, 512), device="cuda")
-    inv2h = torch.from_numpy(2 * step).to("cuda", torch.float32)
-    for v, pose in seen.values():
-        for nb in (1, 13):
-            P = np.concatenate([np.asarray(pose, np.float32).reshape(1, 6)] * nb)
-            E = drr.render_plain_fp32(v, big, torch.from_numpy(P).pin_memory().cuda(non_blocking=True))
-            if nb == 13:  # the same torch ops as a timed gradient request
-                (((E[1:7] - E[7:13]) * g_big).sum(dim=(1, 2)) / inv2h).cpu()
-            E[0].cpu()
-    torch.cuda.synchronize()
-    for v, det, pose, g in reqs:
-        P = np.asarray(pose, np.float32).reshape(1, 6)
-        if g is not None:
-            P = np.concatenate([P, P + np.diag(step).astype(np.float32), P - np.diag(step).astype(np.float32)])
-        P_h = torch.from_numpy(P).pin_memory()
-        g_d = torch.from_numpy(g).cuda() if g is not None else None
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        E = drr.render_plain_fp32(v, det, P_h.cuda(non_blocking=True))
-        if g_d is not None:
-            G = ((E[1:7] - E[7:13]) * g_d).sum(dim=(1, 2)) / inv2h
-            G.cpu()
-        E[0].cpu()
-        b.record()
-        torch.cuda.synchronize()
-        svc.append(a.elapsed_time(b) * 1e-3)
-    span = float(arrivals[-1] - arrivals[0]) if len(arrivals) > 1 else 1.0
-    util = float(np.sum(svc) / max(span, 1e-9))
-    lat = fifo_latencies(arrivals, svc) * 1e3
-    # the same arrival pattern slowed down to half of this server's own capacity
-    lat_half = fifo_latencies(np.asarray(arrivals) * (util / 0.5), svc) * 1e3
-    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "utilisation": util, "stable": util < 1.0,
-            "mean_service_ms": float(np.mean(svc) * 1e3), "p99_service_ms": float(np.percentile(svc, 99) * 1e3),
-            "max_service_ms": float(np.max(svc) * 1e3), "saturation_per_s": float(1.0 / np.mean(svc)),
-            "at_half_own_saturation": {"rate_per_s": float(0.5 / np.mean(svc)),
-                                       "p50_ms": float(np.percentile(lat_half, 50)),
-                                       "p99_ms": float(np.percentile(lat_half, 99))},
-            "what": "same requests and arrival times, one at a time in arrival order: plain FP32 forward walk, "
-                    "gradients by central differences (13 renders per request); device times measured, "
-                    "queue replayed (an unstable queue's latencies grow with the run length)"}
-
-
-def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25, 0.5, 0.8, 0.95)):
-    """Served latency: saturation throughput, then Poisson arrivals at fractions of it."""
+def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25, 0.5, 0.8, 0.95),
+                max_tick_work=SERVE_TICK_WORK, plain=True, vols=None, tick_depth=0):
+    """Served latency: saturation throughput, then Poisson arrivals at fractions of it;
+    beside it the plain FP32 comparison server, measured the same way."""
     import threading
     from paper_2208_12737_gb300 import inputs
-    vols = serving_volumes(drr, hu133)
+    vols = vols or serving_volumes(drr, hu133)
     rng = np.random.default_rng(seed)
     grads = {}
 
@@ -400,33 +335,49 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
             t.wait(120000)
             lat.append(t.result.latency_ms)
 
-    # saturation: everything queued at once; after one untimed pass, the median of
-    # three timed passes over the same requests
+    def new_server(plain_mode=False):
+        if plain_mode:
+            return drr.Server(device_budget=2 << 30, max_inflight=64, plain_fp32_baseline=True)
+        return drr.Server(device_budget=2 << 30, max_inflight=64, use_cuda_graph=True, max_tick_work=max_tick_work,
+                          tick_depth=tick_depth)
+
+    def saturation(reqs, plain_mode=False):
+        """Everything queued at once; after one untimed pass, the median of three timed passes."""
+        srv = new_server(plain_mode)
+        for r in reqs[:32]:
+            srv.submit(*r).wait(120000)
+        drain([srv.submit(*r) for r in reqs], [])
+        rates, lat = [], []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            tickets = [srv.submit(*r) for r in reqs]
+            lat_pass = []
+            drain(tickets, lat_pass)
+            rates.append(len(reqs) / (time.perf_counter() - t0))
+            lat += lat_pass
+        srv.close()
+        return statistics.median(rates), rates, lat
+
     reqs = [make_req() for _ in range(sat_requests)]
-    srv = drr.Server(device_budget=2 << 30, max_inflight=64, use_cuda_graph=True)
-    for r in reqs[:32]:
-        srv.submit(*r).wait(120000)
-    drain([srv.submit(*r) for r in reqs], [])
-    rates, lat_sat = [], []
-    for _ in range(3):
-        t0 = time.perf_counter()
-        tickets = [srv.submit(*r) for r in reqs]
-        lat_pass = []
-        drain(tickets, lat_pass)
-        rates.append(len(reqs) / (time.perf_counter() - t0))
-        lat_sat += lat_pass
-    sat_rate = statistics.median(rates)
-    srv.close()
+    sat_rate, rates, lat_sat = saturation(reqs)
     traces = {}
 
-    def poisson(frac):
-        """Poisson arrivals at frac x the saturation rate for `seconds`; submit->result latencies."""
-        rate = frac * sat_rate
+    def poisson(frac, plain_mode=False, base_rate=None, max_requests=None):
+        """Poisson arrivals at frac x base_rate (default: the saturation rate) for `seconds`;
+        submit->result latencies."""
+        rate = frac * (base_rate or sat_rate)
         n_req = max(50, int(rate * seconds))
-        reqs = [make_req() for _ in range(n_req)]
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
-        traces[frac] = (reqs, arrivals)
-        srv = drr.Server(device_budget=2 << 30, max_inflight=64, use_cuda_graph=True)
+        if max_requests:
+            n_req = min(n_req, max_requests)
+        if plain_mode and base_rate is None and frac in traces:  # the product server's requests and arrival times
+            reqs, arrivals = traces[frac]
+            reqs, arrivals = reqs[:n_req], arrivals[:n_req]
+        else:
+            reqs = [make_req() for _ in range(n_req)]
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+            if not plain_mode:
+                traces[frac] = (reqs, arrivals)
+        srv = new_server(plain_mode)
         for r in reqs[:16]:
             srv.submit(*r).wait(120000)
         lat = []
@@ -470,13 +421,26 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
 
     runs = [poisson(f) for f in loads]
     head = next((r for r in runs if r["load"] == 0.5), runs[0])
-    plain = plain_fifo_server(drr, *traces[head["load"]])
+    plain_res = None
+    if plain:
+        # the comparison server, measured through the same request loop: its own
+        # saturation, Poisson load at half of it, and the product server's headline
+        # request stream (which it cannot keep up with: latencies grow with the run)
+        p_sat, p_rates, _ = saturation(reqs[:300], plain_mode=True)
+        own = poisson(0.5, plain_mode=True, base_rate=p_sat)
+        same = poisson(head["load"], plain_mode=True, max_requests=1000)
+        plain_res = {"saturation_drrs_per_s": p_sat, "saturation_passes_per_s": p_rates,
+                     "at_half_own_saturation": own, "at_product_headline_rate": same,
+                     "what": "drr_server with plain_fp32_baseline: one request per tick, plain FP32 forward walk, "
+                             "gradients by central differences (13 renders per pose); same request mix"}
     return {"p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "mean_ms": head["mean_ms"],
             "requests": head["requests"], "offered_rate_per_s": head["offered_rate_per_s"],
             "achieved_drrs_per_s": head["achieved_drrs_per_s"], "saturation_drrs_per_s": sat_rate,
             "saturation_p50_ms": float(np.percentile(lat_sat, 50)), "saturation_passes_per_s": rates,
             "ticks": head["ticks"],
-            "gpu_busy_frac": head["gpu_busy_frac"], "by_load": runs, "plain_fp32_fifo": plain,
+            "gpu_busy_frac": head["gpu_busy_frac"], "by_load": runs, "plain_fp32_server": plain_res,
+            "max_tick_work": max_tick_work,
+            "tick_depth": tick_depth or 3,
             "workload": "8 resident volumes {128^3, 256^3, 512x512x133, 512x512x300} x {FP32, BF16}; one pose per "
                         "request; detector H=W~U{128..512} at 280/H mm, SDR 510; 50% render+pose-grad; Poisson "
                         "arrivals at the listed fractions of the measured saturation rate (headline: 50%)"}
@@ -664,7 +628,7 @@ def adjoint_bench(drr, vol, det, poses, g, hu_shape, rays, reps=3):
         ms.append(a.elapsed_time(b))
     t = statistics.median(ms)
     return {"ms_per_step": t, "value": rays / (t * 1e-3) / 1e9, "unit": UNIT,
-            "what": "dL/dV by back-projection (exact fixed-point re-walk, FP32 atomics merged down 4x8-tile pixel columns) for the 16-pose batch"}
+            "what": "dL/dV by back-projection (FP32 chunked re-walk, FP32 atomics merged down 4x8-tile pixel columns) for the 16-pose batch"}
 
 
 def fd_baseline(drr, vol, det, poses, rays, reps=3, plain=False):

@@ -262,20 +262,29 @@ drr_status drr_probe_l2_read(const void* buf_dev, size_t bytes, int32_t reps, fl
  * their poses (and upstream gradients), and runs one pose-setup, one persistent
  * ray-walk and one gradient-finalise launch that cover the rays of every
  * admitted request, mixed volumes, dtypes and detectors included (optionally
- * replayed from a captured CUDA graph).  Two ticks can be in flight: requests
- * arriving while one tick runs are admitted into the next.  Results of a request
+ * replayed from a captured CUDA graph).  Several ticks can be in flight
+ * (tick_depth): requests arriving while one tick runs are admitted into the next.  Results of a request
  * are identical whether it ran alone or in a mix (the per-ray arithmetic and the
  * gradient reduction order do not depend on the other requests). */
 
 typedef struct {
   size_t device_budget_bytes; /* device memory reserved for request buffers; 0 -> 512 MiB */
   size_t host_budget_bytes;   /* pinned host staging; 0 -> the device budget */
-  int32_t max_inflight;       /* requests admitted at once (slots); 0 -> 64.  One tick takes at
-                                 most half of the slots and half of each budget (a request that
-                                 needs more goes alone), so the next tick can queue behind it */
+  int32_t max_inflight;       /* requests admitted at once (slots); 0 -> 64 (see tick_depth) */
   int32_t max_tick_poses;     /* poses packed into one tick; 0 -> 4096 (also the largest B accepted) */
   int32_t use_cuda_graph;     /* nonzero: replay the tick's three launches from a captured graph */
   int32_t device;             /* CUDA device ordinal; -1 -> the current device */
+  int64_t max_tick_work;      /* estimated work admitted into one tick, in ray-planes: a request
+                                 counts B*H*W*(nx+ny+nz), times 3/2 with a gradient.  Bounds a
+                                 tick's duration, hence the wait of the requests queued behind it
+                                 (a request larger than the cap goes alone).  0 -> no cap */
+  int32_t plain_fp32_baseline; /* nonzero: the comparison server, not the product: one request per
+                                 tick, rendered by the plain FP32 forward walk
+                                 (drr_render_plain_fp32), a gradient request by central differences
+                                 on it (13 renders per pose, h = 1e-3 rad / 1e-2 mm) */
+  int32_t tick_depth;         /* ticks in flight at once, 2 .. 4; 0 -> 3.  One tick takes at most
+                                 1/tick_depth of the slots and of each budget, so that the next
+                                 ticks can be formed and queued while it runs */
 } drr_server_config;
 
 typedef struct {

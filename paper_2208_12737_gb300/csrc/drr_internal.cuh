@@ -129,6 +129,12 @@ cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom
 // Comparison baseline: the plain FP32 forward walk (out: [B][H][W]).
 cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out,
                                      cudaStream_t stream);
+// Central-difference pose Jacobian from the 13 renders per pose of the plain
+// FP32 comparison server (E13: [B][13][npix], render 0 at the pose, 1 + 2k and
+// 2 + 2k at +h_k and -h_k of parameter k): out [B][npix] = render 0,
+// jac [B][6][npix] = (E(+h_k) - E(-h_k)) / (2 h_k).
+cudaError_t launch_plain_fd_finish(const float* E13, int B, int npix, float h_rot, float h_trans, float* out,
+                                   float* jac, cudaStream_t stream);
 // Negative ZNCC of B moving images against fixed images fixed_stride elements
 // apart (0: one fixed image for all), and optionally d loss / d moving.
 cudaError_t launch_zncc(const float* moving, const float* fixed, size_t fixed_stride, int B, int npix, float eps,

@@ -1695,7 +1695,33 @@ __global__ void __launch_bounds__(256) plain_fp32_kernel(VolumeDev vd, DetDev de
                                                           vd.out_scale;
 }
 
+// The comparison server's central differences (see launch_plain_fd_finish).
+__global__ void plain_fd_finish_kernel(const float* __restrict__ E13, int B, int npix, float h_rot, float h_trans,
+                                       float* __restrict__ out, float* __restrict__ jac) {
+  const int64_t n = static_cast<int64_t>(B) * npix;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int b = static_cast<int>(i / npix);
+    const int p = static_cast<int>(i - static_cast<int64_t>(b) * npix);
+    const float* e = E13 + static_cast<size_t>(b) * 13 * npix + p;
+    out[i] = e[0];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float h2 = 2.f * (k < 3 ? h_rot : h_trans);
+      jac[(static_cast<size_t>(b) * 6 + k) * npix + p] = (e[static_cast<size_t>(1 + 2 * k) * npix] -
+                                                          e[static_cast<size_t>(2 + 2 * k) * npix]) / h2;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_plain_fd_finish(const float* E13, int B, int npix, float h_rot, float h_trans, float* out,
+                                   float* jac, cudaStream_t stream) {
+  plain_fd_finish_kernel<<<grid_for(static_cast<int64_t>(B) * npix, 256), 256, 0, stream>>>(E13, B, npix, h_rot,
+                                                                                          h_trans, out, jac);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out,
                                      cudaStream_t stream) {

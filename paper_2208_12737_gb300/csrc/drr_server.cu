@@ -5,9 +5,10 @@
 // staging) allow, stages their inputs, and runs one pose-setup, one persistent
 // ray-walk and one gradient-finalise launch covering all of their rays; the
 // three launches can be replayed from a CUDA graph captured at start-up (the
-// kernels read the tick's size from a device-resident table).  Up to two ticks
-// are in flight, so requests that arrive while a tick is running are admitted
-// into the next one.  Inputs go up on one copy stream and results come down on
+// kernels read the tick's size from a device-resident table).  Up to
+// tick_depth ticks (3 by default) are in flight, so requests that arrive while
+// a tick is running are admitted into the next one, and an optional cap on the
+// work per tick bounds how long a tick runs.  Inputs go up on one copy stream and results come down on
 // another, ordered against the kernels' stream by events, so a tick's copies
 // overlap the neighbouring ticks' kernels.  A host function enqueued after each
 // tick's result copies marks it finished; the loop then writes results into
@@ -53,11 +54,14 @@ struct Req {
   drr::DetDev det{};
   bool grad = false;
   size_t npix = 0;
+  int64_t work = 0;  // estimated ray-planes (the tick-work cap's unit)
+  int nposes = 0;    // poses rendered: B, or 13 B for a central-difference gradient (comparison server)
   size_t dev_bytes = 0, host_bytes = 0;
   size_t dev_off = 0, host_off = 0;
   bool has_dev = false, has_host = false;
   // device buffers (inside the device arena)
   float *d_poses = nullptr, *d_grad = nullptr, *d_out = nullptr, *d_partials = nullptr, *d_gpose = nullptr;
+  float *d_e13 = nullptr, *d_jac = nullptr;  // comparison server: the 13 renders per pose and the FD Jacobian
   drr::PoseGeom* d_geom = nullptr;
   // pinned staging (inside the host arena)
   float *h_poses = nullptr, *h_grad = nullptr, *h_out = nullptr, *h_gpose = nullptr;
@@ -71,13 +75,15 @@ struct Req {
 
 struct Tick {
   int64_t id = 0;
-  int set = 0;
+  int set = 0;  // the table set (and its events) the tick uses
   std::vector<Req*> reqs;
-  cudaEvent_t start = nullptr, stop = nullptr;  // around the kernels; stop also orders the result copies
-  cudaEvent_t in_ready = nullptr;               // the tick's inputs are on the device
+  bool timed = false;  // its start / stop events were recorded
   std::atomic<bool> done{false};
   struct drr_server_s* owner = nullptr;
 };
+
+// Ticks in flight at once at most (each has its own table set, graph and events).
+constexpr int kMaxTickSets = 4;
 
 // Layout of a tick's work: request i owns the tick's warp tiles
 // [tile_start[i], tile_start[i] + B_i * pose_tiles(det_i)) and poses
@@ -101,24 +107,30 @@ bool layout_tick(int n, const int32_t* B, const drr::DetDev* det, int32_t* tile_
 }
 
 // Sizes of a request's device and staging buffers (each piece 256-B aligned).
-void size_request(Req& q) {
+// The comparison server stages 13 poses per pose of a gradient request, keeps
+// their renders and the FD Jacobian, and gives pose setup its counter slot.
+void size_request(Req& q, bool plain) {
   const size_t B = static_cast<size_t>(q.r.B);
   const size_t nt = static_cast<size_t>(drr::pose_tiles(q.det));  // gradient partials per pose
-  q.dev_bytes = up(B * 6 * 4) + up(B * q.npix * 4) + up(B * sizeof(drr::PoseGeom));
-  q.host_bytes = up(B * 6 * 4) + up(B * q.npix * 4);
+  const size_t P = static_cast<size_t>(q.nposes);
+  q.dev_bytes = up(P * 6 * 4) + up(B * q.npix * 4) + up((P + (plain ? 1 : 0)) * sizeof(drr::PoseGeom));
+  q.host_bytes = up(P * 6 * 4) + up(B * q.npix * 4);
   if (q.grad) {
     q.dev_bytes += up(B * q.npix * 4) + up(B * nt * 6 * 4) + up(B * 6 * 4);
     q.host_bytes += up(B * q.npix * 4) + up(B * 6 * 4);
+    if (plain) q.dev_bytes += up(P * q.npix * 4) + up(B * 6 * q.npix * 4);
   }
 }
+
+// The comparison server's central-difference steps (rad, mm).
+constexpr float kFdRot = 1e-3f, kFdTrans = 1e-2f;
 
 }  // namespace
 
 struct drr_server_s {
   drr_server_config cfg{};
   int device = 0;
-  cudaStream_t stream = nullptr;  // kernels
-  cudaStream_t h2d = nullptr;     // input copies
+  cudaStream_t h2d = nullptr;     // input copies (the kernels run on sets[0].ks)
   cudaStream_t d2h = nullptr;     // result copies
   char* dev_base = nullptr;
   char* host_base = nullptr;
@@ -129,7 +141,11 @@ struct drr_server_s {
     char* d_table = nullptr;
     int* d_counter = nullptr;
     cudaGraphExec_t graph = nullptr;
-  } sets[2];
+    cudaEvent_t start = nullptr, stop = nullptr;  // around the kernels; stop also orders the result copies
+    cudaEvent_t in_ready = nullptr;               // the tick's inputs are on the device
+    cudaStream_t ks = nullptr;                    // the kernel stream (shared by all sets)
+  } sets[kMaxTickSets];
+  int depth = 3;  // ticks in flight at most (table sets in use)
   size_t table_bytes = 0;
   size_t status_off = 0;  // offset of the status words in a table
   int walk_grid = 1;
@@ -156,6 +172,7 @@ struct drr_server_s {
   void finish_tick(Tick* t);
   void sync_streams();
   cudaError_t launch_kernels(int set);
+  cudaError_t launch_plain(const Req& q, cudaStream_t ks);
 };
 
 namespace {
@@ -174,31 +191,50 @@ void CUDART_CB tick_done(void* p) {
 
 cudaError_t drr_server_s::launch_kernels(int set) {
   Set& st = sets[set];
-  if (st.graph) return cudaGraphLaunch(st.graph, stream);
+  if (st.graph) return cudaGraphLaunch(st.graph, st.ks);
   const auto* hdr = reinterpret_cast<const drr::ServeHeader*>(st.d_table);
   const auto* rq = reinterpret_cast<const drr::ServeRequest*>(st.d_table + sizeof(drr::ServeHeader));
   auto* status = reinterpret_cast<unsigned int*>(st.d_table + status_off);
-  return drr::launch_serve_tick(hdr, rq, status, st.d_counter, cfg.max_tick_poses, walk_grid, stream);
+  return drr::launch_serve_tick(hdr, rq, status, st.d_counter, cfg.max_tick_poses, walk_grid, st.ks);
+}
+
+// The comparison server's tick: one request, the plain FP32 forward walk over
+// its poses (13 per pose for a gradient request), then for a gradient the
+// central differences and their sum against the upstream gradient.
+cudaError_t drr_server_s::launch_plain(const Req& q, cudaStream_t ks) {
+  const drr::VolumeDev& vd = q.r.volume->vd;
+  cudaError_t e = drr::launch_pose_setup(q.d_poses, q.nposes, q.det, &vd, q.d_geom, ks);
+  if (e != cudaSuccess) return e;
+  if (!q.grad) return drr::launch_render_plain_fp32(vd, q.det, q.d_geom, q.nposes, q.d_out, ks);
+  e = drr::launch_render_plain_fp32(vd, q.det, q.d_geom, q.nposes, q.d_e13, ks);
+  if (e == cudaSuccess)
+    e = drr::launch_plain_fd_finish(q.d_e13, q.r.B, static_cast<int>(q.npix), kFdRot, kFdTrans, q.d_out, q.d_jac, ks);
+  if (e == cudaSuccess) e = drr::launch_pose_grad_from_jacobian(q.det, q.r.B, q.d_grad, q.d_jac, q.d_gpose, ks);
+  return e;
 }
 
 // Admit requests (FIFO) into a new tick and enqueue it.  Called with lk held;
 // drops it while staging inputs and issuing CUDA calls.
 bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
-  // One tick takes at most half of the request slots and half of each memory
-  // budget (a request that needs more goes alone), so that the next tick can
+  // One tick takes at most 1/depth of the request slots and of each memory
+  // budget (a request that needs more goes alone), so that the next ticks can
   // be formed and queued while this one runs.  Without the cap a backlog puts
   // every slot into one tick, the next tick finds none free until it ends, and
   // the GPU idles between ticks.
-  const int slot_cap = std::max(1, cfg.max_inflight / 2);
+  // The tick-work cap bounds a tick's duration, and with it the wait of the
+  // requests queued behind it; the comparison server takes one request per tick.
+  const int slot_cap = cfg.plain_fp32_baseline ? 1 : std::max(1, cfg.max_inflight / depth);
   std::vector<Req*> batch;
   int poses = 0;
+  int64_t tick_work = 0;
   size_t tick_dev = 0, tick_host = 0;
   while (!pending.empty() && admitted + static_cast<int>(batch.size()) < cfg.max_inflight &&
          static_cast<int>(batch.size()) < slot_cap) {
     Req* q = pending.front();
     if (poses + q->r.B > cfg.max_tick_poses) break;
-    if (!batch.empty() && (tick_dev + q->dev_bytes > cfg.device_budget_bytes / 2 ||
-                           tick_host + q->host_bytes > cfg.host_budget_bytes / 2))
+    if (!batch.empty() && cfg.max_tick_work > 0 && tick_work + q->work > cfg.max_tick_work) break;
+    if (!batch.empty() && (tick_dev + q->dev_bytes > cfg.device_budget_bytes / depth ||
+                           tick_host + q->host_bytes > cfg.host_budget_bytes / depth))
       break;
     size_t doff = 0, hoff = 0;
     if (!dev_arena->alloc(q->dev_bytes, &doff)) break;
@@ -213,6 +249,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     q->state = kAdmitted;
     q->t_admit = Clock::now();
     poses += q->r.B;
+    tick_work += q->work;
     tick_dev += q->dev_bytes;
     tick_host += q->host_bytes;
     batch.push_back(q);
@@ -221,13 +258,11 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   admitted += static_cast<int>(batch.size());
   Tick* t = new Tick();
   t->id = next_tick++;
-  t->set = static_cast<int>(t->id & 1);
+  t->set = static_cast<int>(t->id % depth);
   t->owner = this;
   t->reqs = batch;
   lk.unlock();
-  cudaError_t e = cudaEventCreate(&t->start);
-  if (e == cudaSuccess) e = cudaEventCreate(&t->stop);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->in_ready, cudaEventDisableTiming);
+  cudaError_t e = cudaSuccess;
 
   // carve the buffers and stage the inputs
   Set& st = sets[t->set];
@@ -254,19 +289,38 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     const size_t nt = static_cast<size_t>(drr::pose_tiles(q->det));  // walk tiles and gradient partials per pose
     char* d = dev_base + q->dev_off;
     char* h = host_base + q->host_off;
-    q->d_poses = reinterpret_cast<float*>(d); d += up(B * 6 * 4);
+    const bool plain = cfg.plain_fp32_baseline != 0;
+    const size_t P = static_cast<size_t>(q->nposes);
+    q->d_poses = reinterpret_cast<float*>(d); d += up(P * 6 * 4);
     q->d_out = reinterpret_cast<float*>(d); d += up(B * q->npix * 4);
-    q->d_geom = reinterpret_cast<drr::PoseGeom*>(d); d += up(B * sizeof(drr::PoseGeom));
-    q->h_poses = reinterpret_cast<float*>(h); h += up(B * 6 * 4);
+    q->d_geom = reinterpret_cast<drr::PoseGeom*>(d); d += up((P + (plain ? 1 : 0)) * sizeof(drr::PoseGeom));
+    q->h_poses = reinterpret_cast<float*>(h); h += up(P * 6 * 4);
     q->h_out = reinterpret_cast<float*>(h); h += up(B * q->npix * 4);
     if (q->grad) {
       q->d_grad = reinterpret_cast<float*>(d); d += up(B * q->npix * 4);
       q->d_partials = reinterpret_cast<float*>(d); d += up(B * nt * 6 * 4);
-      q->d_gpose = reinterpret_cast<float*>(d);
+      q->d_gpose = reinterpret_cast<float*>(d); d += up(B * 6 * 4);
+      if (plain) {
+        q->d_e13 = reinterpret_cast<float*>(d); d += up(P * q->npix * 4);
+        q->d_jac = reinterpret_cast<float*>(d);
+      }
       q->h_grad = reinterpret_cast<float*>(h); h += up(B * q->npix * 4);
       q->h_gpose = reinterpret_cast<float*>(h);
     }
-    std::memcpy(q->h_poses, q->r.poses, B * 6 * 4);
+    if (P == B) {
+      std::memcpy(q->h_poses, q->r.poses, B * 6 * 4);
+    } else {  // 13 poses per pose: the pose, then +h and -h of each parameter
+      for (size_t b = 0; b < B; ++b) {
+        for (int c = 0; c < 13; ++c) {
+          float* dst = q->h_poses + (b * 13 + c) * 6;
+          std::memcpy(dst, q->r.poses + b * 6, 6 * 4);
+          if (c > 0) {
+            const int k = (c - 1) / 2;
+            dst[k] += ((c - 1) % 2 == 0 ? 1.f : -1.f) * (k < 3 ? kFdRot : kFdTrans);
+          }
+        }
+      }
+    }
     if (q->grad) std::memcpy(q->h_grad, q->r.grad_drr, B * q->npix * 4);
     drr::ServeRequest& sr = rq[i];
     std::memset(&sr, 0, sizeof(sr));
@@ -291,7 +345,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   const size_t tbytes = sizeof(drr::ServeHeader) + batch.size() * sizeof(drr::ServeRequest);
   const size_t sbytes = batch.size() * sizeof(unsigned int);
   // The table set and the request buffers written here belong to no tick still
-  // in flight: this tick's set was last used two ticks ago, which has finished
+  // in flight: this tick's set was last used `depth` ticks ago, which has finished
   // (its result copies, after its kernels, are done), and the arenas hand out
   // only memory of finished ticks.
   if (e == cudaSuccess) e = cudaMemcpyAsync(st.d_table, st.h_table, tbytes, cudaMemcpyHostToDevice, h2d);
@@ -299,17 +353,23 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     e = cudaMemcpyAsync(st.d_table + status_off, h_status, sbytes, cudaMemcpyHostToDevice, h2d);
   for (Req* q : batch) {
     if (e != cudaSuccess) break;
-    e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->r.B) * 6 * 4, cudaMemcpyHostToDevice, h2d);
+    e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->nposes) * 6 * 4, cudaMemcpyHostToDevice, h2d);
     if (e == cudaSuccess && q->grad)
       e = cudaMemcpyAsync(q->d_grad, q->h_grad, size_t(q->r.B) * q->npix * 4, cudaMemcpyHostToDevice, h2d);
   }
-  if (e == cudaSuccess) e = cudaEventRecord(t->in_ready, h2d);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, t->in_ready, 0);
-  if (e == cudaSuccess) e = cudaEventRecord(t->start, stream);
-  if (e == cudaSuccess) e = launch_kernels(t->set);
-  if (e == cudaSuccess) drr::count_launches(3);
-  if (e == cudaSuccess) e = cudaEventRecord(t->stop, stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, t->stop, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(st.in_ready, h2d);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st.ks, st.in_ready, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(st.start, st.ks);
+  if (cfg.plain_fp32_baseline) {
+    if (e == cudaSuccess) e = launch_plain(*batch[0], st.ks);
+    if (e == cudaSuccess) drr::count_launches(batch[0]->grad ? 4 : 2);
+  } else {
+    if (e == cudaSuccess) e = launch_kernels(t->set);
+    if (e == cudaSuccess) drr::count_launches(3);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(st.stop, st.ks);
+  if (e == cudaSuccess) t->timed = true;
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, st.stop, 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_status, st.d_table + status_off, sbytes, cudaMemcpyDeviceToHost, d2h);
   for (Req* q : batch) {
@@ -323,8 +383,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     // the tick could not be enqueued completely: let what was queued drain, then fail its requests
     sync_streams();
     for (Req* q : batch) q->status = drr::cuda_error(e, "serving tick");
-    if (t->stop) cudaEventDestroy(t->stop);
-    t->stop = nullptr;
+    t->timed = false;
     t->done.store(true);
   }
   lk.lock();
@@ -335,7 +394,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
 
 void drr_server_s::sync_streams() {
   cudaStreamSynchronize(h2d);
-  cudaStreamSynchronize(stream);
+  if (sets[0].ks) cudaStreamSynchronize(sets[0].ks);
   cudaStreamSynchronize(d2h);
 }
 
@@ -359,13 +418,10 @@ void drr_server_s::copy_results(Tick* t) {
 
 // Called with the lock held after copy_results.
 void drr_server_s::finish_tick(Tick* t) {
-  if (t->start && t->stop) {
+  if (t->timed) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, t->start, t->stop) == cudaSuccess) gpu_busy_ms += ms;
+    if (cudaEventElapsedTime(&ms, sets[t->set].start, sets[t->set].stop) == cudaSuccess) gpu_busy_ms += ms;
   }
-  if (t->start) cudaEventDestroy(t->start);
-  if (t->stop) cudaEventDestroy(t->stop);
-  if (t->in_ready) cudaEventDestroy(t->in_ready);
   for (Req* q : t->reqs) {
     if (q->status == DRR_OK) {
       ++completed;
@@ -399,11 +455,11 @@ void drr_server_s::run() {
     }
     if (stop && inflight.empty()) break;
     bool launched = false;
-    if (!stop && !paused && inflight.size() < 2 && !pending.empty()) launched = form_tick(lk);
+    if (!stop && !paused && static_cast<int>(inflight.size()) < depth && !pending.empty()) launched = form_tick(lk);
     if (!launched) {
       cv_loop.wait_for(lk, std::chrono::microseconds(200), [this] {
         return stop || (!inflight.empty() && inflight.front()->done.load()) ||
-               (!paused && inflight.size() < 2 && !pending.empty());
+               (!paused && static_cast<int>(inflight.size()) < depth && !pending.empty());
       });
     }
   }
@@ -422,32 +478,45 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
   if (cfg.max_tick_poses <= 0) cfg.max_tick_poses = 4096;
   if (cfg.max_inflight > 4096 || cfg.max_tick_poses > (1 << 20))
     return drr::set_error(DRR_ERR_INVALID, "max_inflight <= 4096 and max_tick_poses <= 2^20 required");
+  if (cfg.max_tick_work < 0) return drr::set_error(DRR_ERR_INVALID, "max_tick_work must be >= 0");
+  if (cfg.tick_depth == 0) cfg.tick_depth = 3;
+  if (cfg.tick_depth < 2 || cfg.tick_depth > kMaxTickSets)
+    return drr::set_error(DRR_ERR_INVALID, "tick_depth must be in [2, %d]", kMaxTickSets);
   drr_server_s* s = new drr_server_s();
   s->cfg = cfg;
   cudaError_t e = cudaSuccess;
   if (cfg.device >= 0) e = cudaSetDevice(cfg.device);
   if (e == cudaSuccess) e = cudaGetDevice(&s->device);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_base), cfg.device_budget_bytes);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_base), cfg.host_budget_bytes, 0);
   s->status_off = up(sizeof(drr::ServeHeader) + size_t(cfg.max_inflight) * sizeof(drr::ServeRequest));
   s->table_bytes = s->status_off + size_t(cfg.max_inflight) * sizeof(unsigned int);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  s->depth = cfg.tick_depth;
+  for (int i = 0; i < s->depth && e == cudaSuccess; ++i) {
     e = cudaHostAlloc(reinterpret_cast<void**>(&s->sets[i].h_table), s->table_bytes, 0);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->sets[i].d_table), s->table_bytes);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->sets[i].d_counter), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->sets[i].d_table, 0, s->table_bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->sets[i].start);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->sets[i].stop);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->sets[i].in_ready, cudaEventDisableTiming);
+    // one kernel stream for every set: ticks run one after another.  (A stream
+    // per set, so that consecutive ticks overlap, measured slower: saturation
+    // 8.6k-9.2k against 12.1k-13.7k requests/s on the serving mix, the
+    // concurrent walks over different volumes competing for L2.)
+    if (e == cudaSuccess && i == 0) e = cudaStreamCreateWithFlags(&s->sets[0].ks, cudaStreamNonBlocking);
+    s->sets[i].ks = s->sets[0].ks;
   }
   if (e == cudaSuccess) s->walk_grid = drr::serve_walk_grid(s->device);
-  if (e == cudaSuccess && cfg.use_cuda_graph) {
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  if (e == cudaSuccess && cfg.use_cuda_graph && !cfg.plain_fp32_baseline) {
+    for (int i = 0; i < s->depth && e == cudaSuccess; ++i) {
       cudaGraph_t g = nullptr;
-      e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+      e = cudaStreamBeginCapture(s->sets[i].ks, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
         cudaError_t le = s->launch_kernels(i);
-        e = cudaStreamEndCapture(s->stream, &g);
+        e = cudaStreamEndCapture(s->sets[i].ks, &g);
         if (le != cudaSuccess) e = le;
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&s->sets[i].graph, g, 0);
@@ -461,10 +530,13 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
       if (st2.h_table) cudaFreeHost(st2.h_table);
       if (st2.d_table) cudaFree(st2.d_table);
       if (st2.d_counter) cudaFree(st2.d_counter);
+      if (st2.start) cudaEventDestroy(st2.start);
+      if (st2.stop) cudaEventDestroy(st2.stop);
+      if (st2.in_ready) cudaEventDestroy(st2.in_ready);
     }
+    if (s->sets[0].ks) cudaStreamDestroy(s->sets[0].ks);
     if (s->dev_base) cudaFree(s->dev_base);
     if (s->host_base) cudaFreeHost(s->host_base);
-    if (s->stream) cudaStreamDestroy(s->stream);
     if (s->h2d) cudaStreamDestroy(s->h2d);
     if (s->d2h) cudaStreamDestroy(s->d2h);
     delete s;
@@ -499,7 +571,14 @@ drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* tic
     delete q;
     return drr::set_error(DRR_ERR_INVALID, "request has too many tiles");
   }
-  size_request(*q);
+  q->nposes = (s->cfg.plain_fp32_baseline && q->grad) ? 13 * req->B : req->B;
+  if (q->nposes > 65535) {
+    delete q;
+    return drr::set_error(DRR_ERR_INVALID, "the comparison server renders at most 65535 poses per request");
+  }
+  q->work = int64_t(req->B) * int64_t(q->npix) * (int64_t(v->vd.n[0]) + v->vd.n[1] + v->vd.n[2]);
+  if (q->grad) q->work += q->work / 2;
+  size_request(*q, s->cfg.plain_fp32_baseline != 0);
   if (q->dev_bytes > s->cfg.device_budget_bytes || q->host_bytes > s->cfg.host_budget_bytes) {
     size_t need = q->dev_bytes;
     delete q;
@@ -669,10 +748,13 @@ drr_status drr_server_destroy(drr_server s) {
     if (st.h_table) cudaFreeHost(st.h_table);
     if (st.d_table) cudaFree(st.d_table);
     if (st.d_counter) cudaFree(st.d_counter);
+    if (st.start) cudaEventDestroy(st.start);
+    if (st.stop) cudaEventDestroy(st.stop);
+    if (st.in_ready) cudaEventDestroy(st.in_ready);
   }
+  if (s->sets[0].ks) cudaStreamDestroy(s->sets[0].ks);
   cudaFree(s->dev_base);
   cudaFreeHost(s->host_base);
-  cudaStreamDestroy(s->stream);
   cudaStreamDestroy(s->h2d);
   cudaStreamDestroy(s->d2h);
   delete s->dev_arena;

@@ -21,14 +21,3 @@ def test_vectorised_tensor_siddon_matches_oracle():
     r = np.abs(E - ref) / np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
     assert r.max() < 1e-3 and np.median(r) < 1e-5, (r.max(), np.median(r))
     assert np.all(E[ref == 0] == 0)
-
-
-def test_fifo_replay_of_the_plain_serving_baseline():
-    import bench
-    # three requests at once, one unit each: they leave at 1, 2, 3
-    np.testing.assert_allclose(bench.fifo_latencies([0.0, 0.0, 0.0], [1.0, 1.0, 1.0]), [1.0, 2.0, 3.0])
-    # arrivals spaced wider than the service: no waiting
-    np.testing.assert_allclose(bench.fifo_latencies([0.0, 5.0, 9.0], [1.0, 2.0, 0.5]), [1.0, 2.0, 0.5])
-    # a queue that builds and drains
-    np.testing.assert_allclose(bench.fifo_latencies([0.0, 0.5, 1.0, 10.0], [2.0, 2.0, 2.0, 1.0]),
-                               [2.0, 3.5, 5.0, 1.0])

@@ -183,9 +183,9 @@ def test_destroy_with_queued_requests(drr, vols):
 
 
 def test_backlog_is_split_between_two_ticks(drr, vols):
-    # A backlog of small requests: no tick takes more than half of the request
-    # slots, so that the next tick can be formed while one runs; results are
-    # those of the direct calls.
+    # A backlog of small requests: no tick takes more than 1/tick_depth of the
+    # request slots, so that the next ticks can be formed while one runs;
+    # results are those of the direct calls.
     data, sp, vol = vols["a"]
     det = inputs.Detector(300.0, 24, 20, 1.5, 1.5)
     srv = drr.Server(device_budget=64 << 20, max_inflight=16)
@@ -287,3 +287,60 @@ def test_destroy_while_threads_wait(drr, vols):
         th.join(timeout=30)
         assert not th.is_alive()
     assert sorted(codes) == [8] * 6  # all were queued (paused): cancelled
+
+
+def test_tick_work_cap_bounds_each_tick(drr, vols):
+    # a cap of about two requests' work per tick: a backlog of equal requests goes
+    # into ticks of at most two, a request larger than the cap alone, and every
+    # result is the direct call's
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 24, 20, 1.5, 1.5)
+    work = 24 * 20 * (40 + 48 + 56)  # ray-planes of a one-pose render
+    srv = drr.Server(device_budget=64 << 20, max_inflight=32, max_tick_work=2 * work)
+    srv.pause(True)
+    poses = [inputs.random_poses(1, seed=430 + i) for i in range(12)]
+    tickets = [srv.submit(vol, det, p) for p in poses]
+    big = srv.submit(vol, det, inputs.random_poses(3, seed=443))  # 3x the work of one: alone
+    srv.pause(False)
+    outs = [t.wait(20000)[0] for t in tickets]
+    E_big = big.wait(20000)[0]
+    per_tick = {}
+    for t in tickets + [big]:
+        per_tick[t.result.tick] = per_tick.get(t.result.tick, 0) + 1
+    assert max(per_tick.values()) <= 2, per_tick
+    assert per_tick[big.result.tick] == 1
+    for i in (0, 5, 11):
+        np.testing.assert_array_equal(outs[i], _direct(drr, vol, det, poses[i])[0])
+    np.testing.assert_array_equal(E_big, _direct(drr, vol, det, inputs.random_poses(3, seed=443))[0])
+    srv.close()
+
+
+def test_plain_fp32_comparison_server(drr, vols):
+    # the comparison server (one request per tick, plain FP32 walk, central
+    # differences on it): its DRR is the plain walk's, bit for bit, and its
+    # gradient the central differences of plain renders at the same 13 poses
+    data, sp, vol = vols["hu"]
+    det = inputs.Detector(300.0, 33, 29, 1.5, 1.7)
+    srv = drr.Server(device_budget=64 << 20, plain_fp32_baseline=True)
+    P = inputs.random_poses(2, seed=450)
+    g = inputs.upstream_grad((2, 33, 29), seed=451)
+    t_r = srv.submit(vol, det, P)
+    t_g = srv.submit(vol, det, P, g)
+    E_r, _ = t_r.wait(20000)
+    E_g, G = t_g.wait(20000)
+    assert t_r.result.tick != t_g.result.tick  # one request per tick
+    E_plain = drr.render_plain_fp32(vol, det, torch.from_numpy(P).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(E_r, E_plain)
+    np.testing.assert_array_equal(E_g, E_plain)
+    h = np.array([1e-3] * 3 + [1e-2] * 3, np.float32)
+    G_ref = np.zeros((2, 6))
+    for k in range(6):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[:, k] += h[k]
+        Pm[:, k] -= h[k]
+        Ep = drr.render_plain_fp32(vol, det, torch.from_numpy(Pp).cuda()).cpu().numpy().astype(np.float64)
+        Em = drr.render_plain_fp32(vol, det, torch.from_numpy(Pm).cuda()).cpu().numpy().astype(np.float64)
+        G_ref[:, k] = np.sum(g * (Ep - Em), axis=(1, 2)) / (2.0 * np.float64(h[k]))
+    scale = np.abs(G_ref).max(axis=1, keepdims=True)
+    assert np.all(np.abs(G - G_ref) <= 1e-4 * scale), (G, G_ref)
+    srv.close()
