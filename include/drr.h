@@ -287,6 +287,13 @@ typedef struct {
                                  ticks can be formed and queued while it runs */
 } drr_server_config;
 
+/* A request carries the upstream gradient dL/dE itself, not a loss kind: a
+ * loss of the DRR (e.g. -ZNCC against a fixed image) needs the DRR before its
+ * gradient exists, i.e. a second walk in the same tick, while dL/dE supplied
+ * by the caller gives the pose gradient in the tick's single walk.  A
+ * registration step is served as two requests (render, then render+gradient
+ * with dL/dE from drr_zncc), or run directly with drr_render /
+ * drr_render_backward. */
 typedef struct {
   drr_volume volume;        /* must stay alive until the request completes (destroy returns BUSY) */
   drr_detector detector;

@@ -1387,24 +1387,29 @@ __global__ void abs_max_kernel(const void* __restrict__ src, int src_dtype, int6
   if ((threadIdx.x & 31) == 0) atomicMax(out_bits, __float_as_uint(m));
 }
 
-// Element e of the padded storage holds voxel (e / stride_a) mod (n_a + 2) - 1 per
-// axis a, whichever axis the layout makes fastest.
+// One thread per padded voxel (pi, pj, pk): x across the threads of a block,
+// y and z over the grid (grid-stride), written at pi stride_x + pj stride_y +
+// pk stride_z, whichever axis the layout makes fastest; the padding is zero.
 __global__ void ingest_kernel(const void* __restrict__ src, int src_dtype, float mu_water, VolumeDev vd,
                               void* __restrict__ dst, float scale) {
-  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < vd.elems;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>((e / vd.stride[0]) % (vd.n[0] + 2)) - 1;
-    const int j = static_cast<int>((e / vd.stride[1]) % (vd.n[1] + 2)) - 1;
-    const int k = static_cast<int>((e / vd.stride[2]) % (vd.n[2] + 2)) - 1;
-    float v = 0.f;
-    if (i >= 0 && j >= 0 && k >= 0 && i < vd.n[0] && j < vd.n[1] && k < vd.n[2])
-      v = source_value(src, src_dtype, (static_cast<int64_t>(k) * vd.n[1] + j) * vd.n[0] + i, mu_water);
-    if (vd.dtype == kF32) {
-      static_cast<float*>(dst)[e] = v;
-    } else if (vd.dtype == kBF16) {
-      static_cast<__nv_bfloat16*>(dst)[e] = __float2bfloat16_rn(v);
-    } else {
-      static_cast<__half*>(dst)[e] = __float2half_rn(v * scale);
+  const int px = vd.n[0] + 2, py = vd.n[1] + 2, pz = vd.n[2] + 2;
+  const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pi >= px) return;
+  for (int pk = blockIdx.z; pk < pz; pk += gridDim.z) {
+    for (int pj = blockIdx.y; pj < py; pj += gridDim.y) {
+      const int i = pi - 1, j = pj - 1, k = pk - 1;
+      float v = 0.f;
+      if (i >= 0 && j >= 0 && k >= 0 && i < vd.n[0] && j < vd.n[1] && k < vd.n[2])
+        v = source_value(src, src_dtype, (static_cast<int64_t>(k) * vd.n[1] + j) * vd.n[0] + i, mu_water);
+      const int64_t e = static_cast<int64_t>(pi) * vd.stride[0] + static_cast<int64_t>(pj) * vd.stride[1] +
+                        static_cast<int64_t>(pk) * vd.stride[2];
+      if (vd.dtype == kF32) {
+        static_cast<float*>(dst)[e] = v;
+      } else if (vd.dtype == kBF16) {
+        static_cast<__nv_bfloat16*>(dst)[e] = __float2bfloat16_rn(v);
+      } else {
+        static_cast<__half*>(dst)[e] = __float2half_rn(v * scale);
+      }
     }
   }
 }
@@ -1816,7 +1821,8 @@ cudaError_t launch_abs_max(const void* src, int src_dtype, int64_t count, float 
 
 cudaError_t launch_ingest(const void* src, int src_dtype, float mu_water, const VolumeDev& vd, void* dst, float scale,
                           cudaStream_t stream) {
-  ingest_kernel<<<grid_for(vd.elems, 256), 256, 0, stream>>>(src, src_dtype, mu_water, vd, dst, scale);
+  const dim3 grid((vd.n[0] + 2 + 255) / 256, std::min(vd.n[1] + 2, 65535), std::min(vd.n[2] + 2, 65535));
+  ingest_kernel<<<grid, 256, 0, stream>>>(src, src_dtype, mu_water, vd, dst, scale);
   return cudaGetLastError();
 }
 
