@@ -399,8 +399,17 @@ drr_status drr_profile_reset(void);
 /* Total kernel launches issued by the library since it was loaded. */
 int64_t drr_launch_count(void);
 
-/* Synchronise a stream and report any pending device error as DRR_ERR_CUDA. */
+/* Synchronise a stream and report any pending device error as DRR_ERR_CUDA.
+ * In a bounds-checked build, also DRR_ERR_DEVICE when a kernel's bounds check
+ * failed since the last call (the fault word is then cleared). */
 drr_status drr_stream_check(void* cuda_stream);
+
+/* 1 for a bounds-checked build of the library (every voxel gather checked
+ * against the padded volume, every back-projection add against the gradient
+ * volume; a failed check skips the access and is reported by
+ * drr_stream_check), 0 for the product build, which has no checks.  No
+ * counterpart in the paper. */
+int32_t drr_bounds_checked(void);
 
 /* Thread-local message for the last failing call (never NULL). */
 const char* drr_last_error(void);

@@ -553,7 +553,15 @@ drr_status drr_stream_check(void* cuda_stream) {
   if (e != cudaSuccess) return drr::cuda_error(e, "stream");
   e = cudaGetLastError();
   if (e != cudaSuccess) return drr::cuda_error(e, "pending error");
+  unsigned int bits = 0u;
+  e = drr::read_and_clear_fault(&bits);
+  if (e != cudaSuccess) return drr::cuda_error(e, "fault word");
+  if (bits)
+    return drr::set_error(DRR_ERR_DEVICE, "a bounds check failed in a kernel (fault bits 0x%x: 1 gather, 2 back-projection)",
+                          bits);
   return DRR_OK;
 }
+
+int32_t drr_bounds_checked(void) { return drr::bounds_checked() ? 1 : 0; }
 
 }  // extern "C"

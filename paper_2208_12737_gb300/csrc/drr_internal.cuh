@@ -164,6 +164,10 @@ cudaError_t launch_backproject(const VolumeDev& vd, const DetDev& det, const Pos
 int serve_walk_grid(int device);
 cudaError_t launch_serve_tick(const ServeHeader* hdr, const ServeRequest* reqs, unsigned int* status, int* counter,
                               int max_poses, int walk_grid, cudaStream_t stream);
+// Bounds-checked builds: the device fault word (0 in the product build, which
+// has none), read and cleared; and whether this build checks.
+cudaError_t read_and_clear_fault(unsigned int* bits);
+bool bounds_checked();
 // Volume ingest.
 cudaError_t launch_abs_max(const void* src, int src_dtype, int64_t count, float mu_water, unsigned int* out_bits,
                            cudaStream_t stream);

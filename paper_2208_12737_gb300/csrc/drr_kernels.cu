@@ -45,6 +45,31 @@ struct Voxel<kF16> {
   }
 };
 
+// Bounds-checked build (-DDRR_CHECK_BOUNDS=1, a separate library built for
+// tests): every voxel gather is checked against the padded volume and every
+// back-projection add of a live segment against the gradient volume; a check
+// that fails sets a bit of a device-wide fault word (read and cleared by
+// drr_stream_check, which then returns DRR_ERR_DEVICE) and skips the access.
+// The product build has no checks: the zero padding keeps every gather of the
+// walk in bounds, which the checked build verifies on the parity workloads.
+#ifndef DRR_CHECK_BOUNDS
+#define DRR_CHECK_BOUNDS 0
+#endif
+enum FaultBits : unsigned int { kFaultGather = 1u, kFaultBackproject = 2u };
+#if DRR_CHECK_BOUNDS
+__device__ unsigned int g_fault_word = 0u;
+#endif
+template <int DT>
+__device__ __forceinline__ float gather(const VolumeDev& vd, int off) {
+#if DRR_CHECK_BOUNDS
+  if (static_cast<unsigned long long>(static_cast<long long>(off)) >= static_cast<unsigned long long>(vd.elems)) {
+    atomicOr(&g_fault_word, kFaultGather);
+    return 0.f;
+  }
+#endif
+  return Voxel<DT>::load(vd.data, off);
+}
+
 // x_a for a runtime axis index without indexing a register array (which
 // would move the array to local memory).
 template <class T>
@@ -575,7 +600,7 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
   unsigned int kx = 0u, ky = 0u, kz = 0u;  // crossings consumed per axis before this chunk
   unsigned long long O = 0ull;              // exact position of the current point
   int off = r.off;
-  float v = Voxel<DT>::load(vd.data, off);
+  float v = gather<DT>(vd, off);
   float acc = 0.f;
   int remaining = r.nseg - 1;
   const int chunk = fwd_chunk(r.nseg);
@@ -610,12 +635,12 @@ __device__ __forceinline__ float walk_forward(const VolumeDev& vd, const RaySetu
 #endif
     DRR_FSTEP(a1)
     float an1 = a1;
-    float v1 = Voxel<DT>::load(vd.data, off);
+    float v1 = gather<DT>(vd, off);
     float ac = 0.f;
 #pragma unroll kFwdUnroll
     for (int m = 1; m < n; ++m) {
       DRR_FSTEP(an2)
-      const float v2 = Voxel<DT>::load(vd.data, off);
+      const float v2 = gather<DT>(vd, off);
       acc = fmaf(an1 - ac, v, acc);
       ac = an1;
       an1 = an2;
@@ -693,7 +718,7 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
   unsigned int k0 = 0u, k1 = 0u, k2 = 0u;  // crossings taken per slot before this chunk
   unsigned long long O = 0ull;              // exact position of the last crossing taken (the anchor)
   int off = r.off;
-  float v = Voxel<DT>::load(vd.data, off);  // voxel after the pending crossing
+  float v = gather<DT>(vd, off);  // voxel after the pending crossing
   float vprev = 0.f;                        // voxel before it
   float F = 0.f, G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
   // slot of the pending crossing, the last one taken, whose weight is not yet
@@ -742,12 +767,12 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     DRR_JAC_STEP(a1st, b1x, b1y)
     float an1 = a1st;
     bool q0 = b1x, q1 = b1y;
-    float v1 = Voxel<DT>::load(vd.data, off);
+    float v1 = gather<DT>(vd, off);
     float gmin = 3.0e38f;
 #pragma unroll kJacUnroll
     for (int m = 1; m < n; ++m) {
       DRR_JAC_STEP(an2, bx, by)
-      const float v2 = Voxel<DT>::load(vd.data, off);
+      const float v2 = gather<DT>(vd, off);
       const float seg = an1 - ac;
       gmin = fminf(gmin, seg);
       f = fmaf(seg, v, f);
@@ -819,7 +844,7 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
           e2 = --r2 > 0 ? e2 + ws->D[2][t] : ~0ull;
         }
         const float an = local_pos(best, O);
-        const float vn = Voxel<DT>::load(vd.data, off);
+        const float vn = gather<DT>(vd, off);
         f = fmaf(an - ac, v, f);
         ac = an;
         p0 = sx;
@@ -1043,6 +1068,9 @@ __device__ __forceinline__ void walk_backproject(const VolumeDev& vd, const RayS
       const int step = m + j;  // this step ends segment step - 1 (the exit segment at step nseg)
       const float an = fminf(fminf(tx, ty), tz);
       const float val = s * ((step < nseg ? an : xe) - ac);
+#if DRR_CHECK_BOUNDS
+      if (step <= nseg && lin >= nvox) atomicOr(&g_fault_word, kFaultBackproject);
+#endif
       red_column_merged<kBpTileW>(gvol, step <= nseg ? lin : 0xffffffffu, val, nvox, lane);
       ac = an;
       const bool bx = tx == an;
@@ -1720,6 +1748,21 @@ __global__ void plain_fd_finish_kernel(const float* __restrict__ E13, int B, int
 }
 
 }  // namespace
+
+cudaError_t read_and_clear_fault(unsigned int* bits) {
+  *bits = 0u;
+#if DRR_CHECK_BOUNDS
+  cudaError_t e = cudaMemcpyFromSymbol(bits, g_fault_word, sizeof(unsigned int));
+  if (e != cudaSuccess) return e;
+  const unsigned int zero = 0u;
+  if (*bits) e = cudaMemcpyToSymbol(g_fault_word, &zero, sizeof(unsigned int));
+  return e;
+#else
+  return cudaSuccess;
+#endif
+}
+
+bool bounds_checked() { return DRR_CHECK_BOUNDS != 0; }
 
 cudaError_t launch_plain_fd_finish(const float* E13, int B, int npix, float h_rot, float h_trans, float* out,
                                    float* jac, cudaStream_t stream) {

@@ -31,7 +31,7 @@ EXPORTS = (
     "drr_server_pause", "drr_server_destroy", "drr_arena_create", "drr_arena_alloc", "drr_arena_free", "drr_arena_in_use",
     "drr_arena_largest_free", "drr_arena_destroy", "drr_pose_grad_noalloc", "drr_zncc", "drr_adam_step",
     "drr_loss_landscape", "drr_geometry_grad", "drr_probe_l2_read", "drr_render_plain_fp32",
-    "drr_server_poll", "drr_server_inject_device_status", "drr_serve_tick_layout",
+    "drr_server_poll", "drr_server_inject_device_status", "drr_serve_tick_layout", "drr_bounds_checked",
 )
 
 
@@ -83,12 +83,16 @@ _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 
 
-def load(path: str = LIB_PATH):
-    """Load libdrr.so and declare its signatures.  Raises if it is missing."""
+def load(path: str = None):
+    """Load libdrr.so and declare its signatures.  Raises if it is missing.
+    DRR_LIBRARY in the environment names another build of the same ABI (the
+    tests load the bounds-checked one this way)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
+        if path is None:
+            path = os.environ.get("DRR_LIBRARY") or LIB_PATH
         if not os.path.exists(path):
             raise FileNotFoundError(f"libdrr not built: {path} is missing (run paper_2208_12737_gb300.build.build())")
         lib = ctypes.CDLL(path)
@@ -142,6 +146,8 @@ def load(path: str = LIB_PATH):
             if name not in ("drr_last_error", "drr_version"):
                 getattr(lib, name).restype = ctypes.c_int
         lib.drr_launch_count.restype = ctypes.c_int64
+        lib.drr_bounds_checked.argtypes = []
+        lib.drr_bounds_checked.restype = ctypes.c_int32
         lib.drr_arena_in_use.restype = ctypes.c_size_t
         lib.drr_arena_largest_free.restype = ctypes.c_size_t
         _lib = lib

@@ -17,3 +17,17 @@ def golden():
     import json
     with open(os.path.join(ROOT, "tests", "golden", "worked_examples.json")) as f:
         return json.load(f)
+
+
+@pytest.fixture(autouse=True)
+def _bounds_checked_library(request):
+    """With DRR_LIBRARY naming the bounds-checked build, every GPU test ends by
+    checking that no kernel's bounds check failed during it."""
+    yield
+    if not os.environ.get("DRR_LIBRARY") or request.node.get_closest_marker("gpu") is None:
+        return
+    from paper_2208_12737_gb300 import drr
+    lib = drr.load()
+    assert lib.drr_bounds_checked() == 1
+    st = lib.drr_stream_check(None)
+    assert st == 0, lib.drr_last_error().decode()
