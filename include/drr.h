@@ -138,6 +138,10 @@ drr_status drr_volume_info(drr_volume v, int32_t dims[3], float spacing[3], drr_
  *  jac_out_dev : NULL, or [B][6][H][W] float32 (planar) overwritten with
  *                dE/d eta_k per pixel (Sec. 2.4 gradient, voxel lookup held
  *                fixed), for a later drr_render_backward.
+ * With a Jacobian, a launch too small to fill the GPU (up to a few hundred
+ * 8x4-pixel tiles, e.g. one 128x128 pose) walks each ray on 4 or 8 warps, each
+ * taking a run of the ray's chunks; the results are the same bits as the
+ * one-lane walk's.
  * Errors: DRR_ERR_INVALID, DRR_ERR_OOM, DRR_ERR_CUDA. */
 drr_status drr_render(drr_volume v, const drr_detector* det, const float* poses_dev, int32_t B,
                       float* drr_out_dev, float* jac_out_dev, void* cuda_stream);
@@ -389,7 +393,9 @@ drr_status drr_arena_destroy(drr_arena a);
 /* While enabled, every kernel launch is bracketed by CUDA events recorded on
  * its stream.  Kernel names: "pose_setup", "siddon_fwd", "siddon_fwd_jac",
  * "siddon_pose_grad", "jac_reduce", "pose_grad_finalize", "siddon_backproject",
- * "count_segments". */
+ * "count_segments", "zncc", "siddon_geometry_grad", "plain_fp32_fwd",
+ * "siddon_fwd_jac_split" (a fused forward + Jacobian launch small enough to
+ * walk each ray on 4 or 8 lanes; same results as "siddon_fwd_jac"). */
 drr_status drr_profile_enable(int32_t on);
 /* Synchronise the recorded events and return the summed device time (ms) and
  * the number of launches of one kernel since the last reset. */

@@ -120,12 +120,12 @@ struct AsyncBuf {
 // ---- kernel timing: CUDA events around each launch while enabled ----------
 enum ProfKernel {
   kPoseSetup, kSiddonFwd, kSiddonFwdJac, kSiddonPoseGrad, kJacReduce, kFinalize, kBackproject, kCountSeg, kZncc,
-  kSiddonGeoGrad, kPlainFp32, kNumProf
+  kSiddonGeoGrad, kPlainFp32, kSiddonFwdJacSplit, kNumProf
 };
 const char* const kProfNames[kNumProf] = {"pose_setup",        "siddon_fwd", "siddon_fwd_jac",     "siddon_pose_grad",
                                           "jac_reduce",        "pose_grad_finalize", "siddon_backproject",
                                           "count_segments",    "zncc",       "siddon_geometry_grad",
-                                          "plain_fp32_fwd"};
+                                          "plain_fp32_fwd",    "siddon_fwd_jac_split"};
 struct ProfRecord {
   int kernel;
   cudaEvent_t start, stop;
@@ -415,8 +415,9 @@ drr_status drr_render(drr_volume v, const drr_detector* det, const float* poses_
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
   if (drr_status s = setup_geometry(v, dd, poses_dev, B, st, pg)) return s;
-  LaunchScope ls(jac_out_dev ? kSiddonFwdJac : kSiddonFwd, st);
-  DRR_CUDA(drr::launch_render(v->vd, dd, pg.p, B, drr_out_dev, jac_out_dev, st), "render launch");
+  const int lanes = jac_out_dev ? drr::render_split_lanes(v->vd, dd, B) : 1;
+  LaunchScope ls(jac_out_dev ? (lanes > 1 ? kSiddonFwdJacSplit : kSiddonFwdJac) : kSiddonFwd, st);
+  DRR_CUDA(drr::launch_render(v->vd, dd, pg.p, B, drr_out_dev, jac_out_dev, st, lanes), "render launch");
   return DRR_OK;
 }
 

@@ -124,8 +124,11 @@ enum ServeStatusBits : unsigned int {
 cudaError_t launch_pose_setup(const float* poses, int B, const DetDev& det, const VolumeDev* vd, PoseGeom* out,
                               cudaStream_t stream);
 cudaError_t launch_ray_setup(const float* poses, int B, const DetDev& det, float* rays, cudaStream_t stream);
+// lanes: 1 = one lane per ray; 4 or 8 = the split walk (fused forward +
+// Jacobian only), as render_split_lanes chooses for the launch.
 cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
-                          cudaStream_t stream);
+                          cudaStream_t stream, int lanes = 1);
+int render_split_lanes(const VolumeDev& vd, const DetDev& det, int B);
 // Comparison baseline: the plain FP32 forward walk (out: [B][H][W]).
 cudaError_t launch_render_plain_fp32(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out,
                                      cudaStream_t stream);

@@ -693,53 +693,89 @@ struct JacSums {
 constexpr float kTieRel = 2.98023223876953125e-7f;  // 1.25 * 2^-22
 constexpr float kTieAbs = 9.765625e-4f;             // 2^-10 high-word units
 
-template <int DT>
-__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, JacScratch* ws,
-                                              JacSums& out) {
+// Per-ray constants of the Jacobian walk: the slot relabelling (slot 2 is the
+// axis with most crossings), each slot's signed stride and FP32 plane spacing,
+// and the chunk length.  jac_prepare also stores each slot's exact sequence
+// (first crossing, spacing, count) in the lane's shared-memory scratch.
+struct JacRay {
+  int dom, a0, a1;
+  int step[3];
+  float dl[3];
+  int chunk;
+};
+
+// State of the Jacobian walk at a chunk boundary.
+struct JacState {
+  unsigned int k0, k1, k2;  // crossings taken per slot
+  unsigned long long O;     // exact position of the last crossing taken (the anchor)
+  int off;                  // voxel after it (padded offset)
+  float v, vprev;           // voxel after and before it
+  bool p0, p1;              // its slot (neither: slot 2 or a clamped entry), whose weight is not yet summed
+};
+
+// One chunk's contribution: the segment sum f (its last segment ending at the
+// exact anchor of the next chunk) and the two slots' weight sums in local
+// positions, with the chunk's anchor as FP32 (Of).
+struct JacChunk {
+  float f, g0, g1, h0, h1, Of;
+};
+
+__device__ __forceinline__ void jac_prepare(const RaySetup& r, JacScratch* ws, JacRay& jr) {
   const int t = threadIdx.x;
   int dom = 0;
   if (r.cnt[1] > r.cnt[dom]) dom = 1;
   if (r.cnt[2] > r.cnt[dom]) dom = 2;
-  const int a0 = dom == 0 ? 1 : 0;  // real axis of slot 0
-  const int a1 = dom == 2 ? 1 : 2;  // real axis of slot 1
-  const int ax_of[3] = {a0, a1, dom};
-  int step[3];
-  float dl[3];
+  jr.dom = dom;
+  jr.a0 = dom == 0 ? 1 : 0;  // real axis of slot 0
+  jr.a1 = dom == 2 ? 1 : 2;  // real axis of slot 1
+  const int ax_of[3] = {jr.a0, jr.a1, dom};
 #pragma unroll
   for (int sl = 0; sl < 3; ++sl) {
     const int a = ax_of[sl];
     const unsigned long long D = pick3(a, r.D[0], r.D[1], r.D[2]);
     ws->A0[sl][t] = pick3(a, r.A0[0], r.A0[1], r.A0[2]);
     ws->D[sl][t] = D;
-    step[sl] = pick3(a, r.step[0], r.step[1], r.step[2]);
+    jr.step[sl] = pick3(a, r.step[0], r.step[1], r.step[2]);
     ws->cnt[sl][t] = pick3(a, r.cnt[0], r.cnt[1], r.cnt[2]);
-    dl[sl] = fix_to_float(static_cast<long long>(D));
+    jr.dl[sl] = fix_to_float(static_cast<long long>(D));
   }
-  unsigned int k0 = 0u, k1 = 0u, k2 = 0u;  // crossings taken per slot before this chunk
-  unsigned long long O = 0ull;              // exact position of the last crossing taken (the anchor)
-  int off = r.off;
-  float v = gather<DT>(vd, off);  // voxel after the pending crossing
-  float vprev = 0.f;                        // voxel before it
-  float F = 0.f, G0 = 0.f, G1 = 0.f, A0 = 0.f, A1 = 0.f, Gc = 0.f;
-  // slot of the pending crossing, the last one taken, whose weight is not yet
-  // summed (neither: slot 2 or a clamped entry); it sits at the anchor
-  bool p0 = r.ea == a0, p1 = r.ea == a1;
-  if (r.ea < 0) Gc = -v;  // entry clamped at alpha 0: weight -V_first
-  int remaining = r.nseg - 1;
-  const int chunk = walk_chunk(r.nseg);
-  while (remaining > 0) {
-    const int n = min(remaining, chunk);
-    ws->c_off[t] = off;
-    ws->c_v[t] = v;
-    ws->c_vprev[t] = vprev;
-    ws->c_pend[t] = p0 ? 0 : (p1 ? 1 : 2);
-    const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], k0), O);
-    const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], k1), O);
-    const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], k2), O);
-    float tx = x0, ty = y0, tz = z0;
-    float lx = 0.f, ly = 0.f, lz = 0.f;
-    // chunk sums in local positions
-    float ac = 0.f, f = 0.f, g0 = 0.f, g1 = 0.f, h0 = 0.f, h1 = 0.f;
+  jr.chunk = walk_chunk(r.nseg);
+}
+
+// The state before the first crossing: the entry voxel, the entry crossing pending.
+template <int DT>
+__device__ __forceinline__ void jac_start(const VolumeDev& vd, const RaySetup& r, const JacRay& jr, JacState& s) {
+  s.k0 = s.k1 = s.k2 = 0u;
+  s.O = 0ull;
+  s.off = r.off;
+  s.v = gather<DT>(vd, s.off);
+  s.vprev = 0.f;
+  s.p0 = r.ea == jr.a0;
+  s.p1 = r.ea == jr.a1;
+}
+
+// One chunk of n crossings from state s (more: crossings follow the chunk).
+template <int DT>
+__device__ __forceinline__ void jac_chunk(const VolumeDev& vd, const JacRay& jr, JacScratch* ws, JacState& s, int n,
+                                          bool more, JacChunk& out) {
+  const int t = threadIdx.x;
+  const int* step = jr.step;
+  const float* dl = jr.dl;
+  unsigned long long O = s.O;
+  int off = s.off;
+  float v = s.v, vprev = s.vprev;
+  bool p0 = s.p0, p1 = s.p1;
+  ws->c_off[t] = off;
+  ws->c_v[t] = v;
+  ws->c_vprev[t] = vprev;
+  ws->c_pend[t] = p0 ? 0 : (p1 ? 1 : 2);
+  const float x0 = local_pos(fix_at(ws->A0[0][t], ws->D[0][t], s.k0), O);
+  const float y0 = local_pos(fix_at(ws->A0[1][t], ws->D[1][t], s.k1), O);
+  const float z0 = local_pos(fix_at(ws->A0[2][t], ws->D[2][t], s.k2), O);
+  float tx = x0, ty = y0, tz = z0;
+  float lx = 0.f, ly = 0.f, lz = 0.f;
+  // chunk sums in local positions
+  float ac = 0.f, f = 0.f, g0 = 0.f, g1 = 0.f, h0 = 0.f, h1 = 0.f;
 #define DRR_JAC_STEP(an, bx, by)                           \
   const float an = fminf(fminf(tx, ty), tz);               \
   const bool bx = tx == an;                                \
@@ -759,148 +795,190 @@ __device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetu
     if (p0) { g0 += wgt; h0 = fmaf(wgt, ac, h0); }         \
     if (p1) { g1 += wgt; h1 = fmaf(wgt, ac, h1); }         \
   }
-    // The gathers run two crossings ahead: crossing m+1 (an1, q0/q1, voxel v1
-    // after it) is taken while segment m is summed, and a crossing's weight is
-    // taken once the voxel after it has had one walk step to arrive.  First the
-    // pending crossing at the anchor.
-    DRR_JAC_ACCOUNT()
-    DRR_JAC_STEP(a1st, b1x, b1y)
-    float an1 = a1st;
-    bool q0 = b1x, q1 = b1y;
-    float v1 = gather<DT>(vd, off);
-    float gmin = 3.0e38f;
+  // The gathers run two crossings ahead: crossing m+1 (an1, q0/q1, voxel v1
+  // after it) is taken while segment m is summed, and a crossing's weight is
+  // taken once the voxel after it has had one walk step to arrive.  First the
+  // pending crossing at the anchor.
+  DRR_JAC_ACCOUNT()
+  DRR_JAC_STEP(a1st, b1x, b1y)
+  float an1 = a1st;
+  bool q0 = b1x, q1 = b1y;
+  float v1 = gather<DT>(vd, off);
+  float gmin = 3.0e38f;
 #pragma unroll kJacUnroll
-    for (int m = 1; m < n; ++m) {
-      DRR_JAC_STEP(an2, bx, by)
-      const float v2 = gather<DT>(vd, off);
-      const float seg = an1 - ac;
-      gmin = fminf(gmin, seg);
-      f = fmaf(seg, v, f);
-      {  // crossing m, at the end of the segment just summed
-        const float wgt = v - v1;
-        if (q0) { g0 += wgt; h0 = fmaf(wgt, an1, h0); }
-        if (q1) { g1 += wgt; h1 = fmaf(wgt, an1, h1); }
-      }
-      ac = an1;
-      q0 = bx;
-      q1 = by;
-      v = v1;
-      v1 = v2;
-      an1 = an2;
-    }
-    // drain: the segment that ends at the chunk's last crossing, which stays pending
-    {
-      const float seg = an1 - ac;
-      gmin = fminf(gmin, seg);
-      f = fmaf(seg, v, f);
+  for (int m = 1; m < n; ++m) {
+    DRR_JAC_STEP(an2, bx, by)
+    const float v2 = gather<DT>(vd, off);
+    const float seg = an1 - ac;
+    gmin = fminf(gmin, seg);
+    f = fmaf(seg, v, f);
+    {  // crossing m, at the end of the segment just summed
+      const float wgt = v - v1;
+      if (q0) { g0 += wgt; h0 = fmaf(wgt, an1, h0); }
+      if (q1) { g1 += wgt; h1 = fmaf(wgt, an1, h1); }
     }
     ac = an1;
-    p0 = q0;
-    p1 = q1;
-    vprev = v;
+    q0 = bx;
+    q1 = by;
     v = v1;
-    unsigned int c0 = static_cast<unsigned int>(lx), c1 = static_cast<unsigned int>(ly),
-                 c2 = static_cast<unsigned int>(lz);
-    // The float order is exact unless two crossings came within the FP32 error
-    // of the local positions: check the chunk's shortest segment and the gap to
-    // the next crossing after it.
-    const float next = fminf(fminf(tx, ty), tz);
-    if (gmin < fmaf(ac, kTieRel, kTieAbs) || (remaining > n && next - ac < fmaf(next, kTieRel, kTieAbs))) {
-      // exact re-walk of the chunk: the next crossing of each slot held as 64-bit
-      // fixed point (all ones once the slot's crossings are used up), the
-      // smallest taken each step (ties to the lower slot)
-      off = ws->c_off[t];
-      v = ws->c_v[t];
-      vprev = ws->c_vprev[t];
-      const int pend = ws->c_pend[t];
-      p0 = pend == 0;
-      p1 = pend == 1;
-      ac = f = g0 = g1 = h0 = h1 = 0.f;
-      c0 = c1 = c2 = 0u;
-      int r0 = ws->cnt[0][t] - static_cast<int>(k0), r1 = ws->cnt[1][t] - static_cast<int>(k1),
-          r2 = ws->cnt[2][t] - static_cast<int>(k2);
-      unsigned long long e0 = r0 > 0 ? fix_at(ws->A0[0][t], ws->D[0][t], k0) : ~0ull;
-      unsigned long long e1 = r1 > 0 ? fix_at(ws->A0[1][t], ws->D[1][t], k1) : ~0ull;
-      unsigned long long e2 = r2 > 0 ? fix_at(ws->A0[2][t], ws->D[2][t], k2) : ~0ull;
-      for (int m = 0; m < n; ++m) {
-        DRR_JAC_ACCOUNT()
-        const bool sx = e0 <= e1 && e0 <= e2;
-        const bool sy = !sx && e1 <= e2;
-        unsigned long long best;
-        if (sx) {
-          best = e0;
-          off += step[0];
-          ++c0;
-          e0 = --r0 > 0 ? e0 + ws->D[0][t] : ~0ull;
-        } else if (sy) {
-          best = e1;
-          off += step[1];
-          ++c1;
-          e1 = --r1 > 0 ? e1 + ws->D[1][t] : ~0ull;
-        } else {
-          best = e2;
-          off += step[2];
-          ++c2;
-          e2 = --r2 > 0 ? e2 + ws->D[2][t] : ~0ull;
-        }
-        const float an = local_pos(best, O);
-        const float vn = gather<DT>(vd, off);
-        f = fmaf(an - ac, v, f);
-        ac = an;
-        p0 = sx;
-        p1 = sy;
-        vprev = v;
-        v = vn;
+    v1 = v2;
+    an1 = an2;
+  }
+  // drain: the segment that ends at the chunk's last crossing, which stays pending
+  {
+    const float seg = an1 - ac;
+    gmin = fminf(gmin, seg);
+    f = fmaf(seg, v, f);
+  }
+  ac = an1;
+  p0 = q0;
+  p1 = q1;
+  vprev = v;
+  v = v1;
+  unsigned int c0 = static_cast<unsigned int>(lx), c1 = static_cast<unsigned int>(ly),
+               c2 = static_cast<unsigned int>(lz);
+  // The float order is exact unless two crossings came within the FP32 error
+  // of the local positions: check the chunk's shortest segment and the gap to
+  // the next crossing after it.
+  const float next = fminf(fminf(tx, ty), tz);
+  if (gmin < fmaf(ac, kTieRel, kTieAbs) || (more && next - ac < fmaf(next, kTieRel, kTieAbs))) {
+    // exact re-walk of the chunk: the next crossing of each slot held as 64-bit
+    // fixed point (all ones once the slot's crossings are used up), the
+    // smallest taken each step (ties to the lower slot)
+    off = ws->c_off[t];
+    v = ws->c_v[t];
+    vprev = ws->c_vprev[t];
+    const int pend = ws->c_pend[t];
+    p0 = pend == 0;
+    p1 = pend == 1;
+    ac = f = g0 = g1 = h0 = h1 = 0.f;
+    c0 = c1 = c2 = 0u;
+    int r0 = ws->cnt[0][t] - static_cast<int>(s.k0), r1 = ws->cnt[1][t] - static_cast<int>(s.k1),
+        r2 = ws->cnt[2][t] - static_cast<int>(s.k2);
+    unsigned long long e0 = r0 > 0 ? fix_at(ws->A0[0][t], ws->D[0][t], s.k0) : ~0ull;
+    unsigned long long e1 = r1 > 0 ? fix_at(ws->A0[1][t], ws->D[1][t], s.k1) : ~0ull;
+    unsigned long long e2 = r2 > 0 ? fix_at(ws->A0[2][t], ws->D[2][t], s.k2) : ~0ull;
+    for (int m = 0; m < n; ++m) {
+      DRR_JAC_ACCOUNT()
+      const bool sx = e0 <= e1 && e0 <= e2;
+      const bool sy = !sx && e1 <= e2;
+      unsigned long long best;
+      if (sx) {
+        best = e0;
+        off += step[0];
+        ++c0;
+        e0 = --r0 > 0 ? e0 + ws->D[0][t] : ~0ull;
+      } else if (sy) {
+        best = e1;
+        off += step[1];
+        ++c1;
+        e1 = --r1 > 0 ? e1 + ws->D[1][t] : ~0ull;
+      } else {
+        best = e2;
+        off += step[2];
+        ++c2;
+        e2 = --r2 > 0 ? e2 + ws->D[2][t] : ~0ull;
       }
+      const float an = local_pos(best, O);
+      const float vn = gather<DT>(vd, off);
+      f = fmaf(an - ac, v, f);
+      ac = an;
+      p0 = sx;
+      p1 = sy;
+      vprev = v;
+      v = vn;
     }
+  }
 #undef DRR_JAC_STEP
 #undef DRR_JAC_ACCOUNT
-    remaining -= n;
-    k0 += c0;
-    k1 += c1;
-    k2 += c2;
-    // the chunk's last crossing (the largest one taken) is the next anchor; the
-    // segment that ends there gets its exact end
-    unsigned long long Onew = O;
-    if (k0) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], k0 - 1u));
-    if (k1) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], k1 - 1u));
-    if (k2) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], k2 - 1u));
-    f = fmaf(local_pos(Onew, O) - ac, vprev, f);
-    // chunk sums to absolute positions: alpha = O + local
-    const float Of = fix_to_float(static_cast<long long>(O));
-    F += f;
-    G0 += g0;
-    A0 += fmaf(Of, g0, h0);
-    G1 += g1;
-    A1 += fmaf(Of, g1, h1);
-    O = Onew;
-  }
-  // the last segment, from the last crossing (the anchor) to the exit, and the
-  // last crossing's weight at its absolute position
-  F = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, O), v, F);
+  s.k0 += c0;
+  s.k1 += c1;
+  s.k2 += c2;
+  // the chunk's last crossing (the largest one taken) is the next anchor; the
+  // segment that ends there gets its exact end
+  unsigned long long Onew = O;
+  if (s.k0) Onew = max(Onew, fix_at(ws->A0[0][t], ws->D[0][t], s.k0 - 1u));
+  if (s.k1) Onew = max(Onew, fix_at(ws->A0[1][t], ws->D[1][t], s.k1 - 1u));
+  if (s.k2) Onew = max(Onew, fix_at(ws->A0[2][t], ws->D[2][t], s.k2 - 1u));
+  out.f = fmaf(local_pos(Onew, O) - ac, vprev, f);
+  out.g0 = g0;
+  out.g1 = g1;
+  out.h0 = h0;
+  out.h1 = h1;
+  out.Of = fix_to_float(static_cast<long long>(O));
+  s.O = Onew;
+  s.off = off;
+  s.v = v;
+  s.vprev = vprev;
+  s.p0 = p0;
+  s.p1 = p1;
+}
+
+// Running sums of the Jacobian walk over its chunks, in chunk order (chunk sums
+// to absolute positions: alpha = O + local).
+struct JacTotals {
+  float F, G0, G1, A0, A1;
+};
+
+__device__ __forceinline__ void jac_add_chunk(JacTotals& T, const JacChunk& c) {
+  T.F += c.f;
+  T.G0 += c.g0;
+  T.A0 += fmaf(c.Of, c.g0, c.h0);
+  T.G1 += c.g1;
+  T.A1 += fmaf(c.Of, c.g1, c.h1);
+}
+
+// After the last chunk: the last segment to the exit, the last crossing's
+// weight at its absolute position, the exit crossing, and the sums moved back
+// to alpha units and real axes.  Gc: the clamped entry's weight.
+__device__ __forceinline__ void jac_finish(const RaySetup& r, const JacRay& jr, const JacState& s, JacTotals T,
+                                           float Gc, JacSums& out) {
+  float F = fmaf(local_pos(static_cast<unsigned long long>(kExitUnits) << 32, s.O), s.v, T.F);
+  float G0 = T.G0, G1 = T.G1, A0 = T.A0, A1 = T.A1;
   {
-    const float last = fix_to_float(static_cast<long long>(O));
-    const float wgt = vprev - v;
-    if (p0) { G0 += wgt; A0 = fmaf(wgt, last, A0); }
-    if (p1) { G1 += wgt; A1 = fmaf(wgt, last, A1); }
+    const float last = fix_to_float(static_cast<long long>(s.O));
+    const float wgt = s.vprev - s.v;
+    if (s.p0) { G0 += wgt; A0 = fmaf(wgt, last, A0); }
+    if (s.p1) { G1 += wgt; A1 = fmaf(wgt, last, A1); }
   }
   // exit crossing: weight V_last - 0 at the exit
+  const float v = s.v;
   const float ex = static_cast<float>(kExitUnits);
   float Ac = 0.f;
   if (r.xa < 0) { Gc += v; Ac = v * ex; }
-  else if (r.xa == a0) { G0 += v; A0 = fmaf(v, ex, A0); }
-  else if (r.xa == a1) { G1 += v; A1 = fmaf(v, ex, A1); }
+  else if (r.xa == jr.a0) { G0 += v; A0 = fmaf(v, ex, A0); }
+  else if (r.xa == jr.a1) { G1 += v; A1 = fmaf(v, ex, A1); }
   // back to alpha units and real axes (static indices)
   const float u = r.unit;
   out.F = F * u;
-  out.dom = dom;
+  out.dom = jr.dom;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    out.G[a] = a == a0 ? G0 : (a == a1 ? G1 : -(G0 + G1 + Gc));  // sum of all crossing weights is 0
-    out.A[a] = a == a0 ? A0 * u : (a == a1 ? A1 * u : 0.f);      // the dominant axis is handled through R
+    out.G[a] = a == jr.a0 ? G0 : (a == jr.a1 ? G1 : -(G0 + G1 + Gc));  // sum of all crossing weights is 0
+    out.A[a] = a == jr.a0 ? A0 * u : (a == jr.a1 ? A1 * u : 0.f);      // the dominant axis is handled through R
   }
   out.Gc = Gc;
   out.Ac = Ac * u;
+}
+
+template <int DT>
+__device__ __forceinline__ void walk_jacobian(const VolumeDev& vd, const RaySetup& r, JacScratch* ws,
+                                              JacSums& out) {
+  JacRay jr;
+  jac_prepare(r, ws, jr);
+  JacState s;
+  jac_start<DT>(vd, r, jr, s);
+  const float Gc = r.ea < 0 ? -s.v : 0.f;  // entry clamped at alpha 0: weight -V_first
+  JacTotals T{0.f, 0.f, 0.f, 0.f, 0.f};
+  int remaining = r.nseg - 1;
+  while (remaining > 0) {
+    const int n = min(remaining, jr.chunk);
+    JacChunk c;
+    jac_chunk<DT>(vd, jr, ws, s, n, remaining > n, c);
+    remaining -= n;
+    jac_add_chunk(T, c);
+  }
+  jac_finish(r, jr, s, T, Gc, out);
 }
 
 // dE/d eta for one ray from the crossing sums (Sec. 2.4 with the voxel lookup
@@ -1257,6 +1335,172 @@ __global__ void __launch_bounds__(kThreads, (MODE == kFwdJac || MODE == kPoseGra
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split walk for launches too small to fill the GPU (the fused forward +
+// pose-Jacobian mode): each ray is walked by K lanes, lane j taking the j-th
+// of K runs of whole chunks.  A lane rebuilds the exact walk state at its first
+// chunk boundary, walks its chunks with the same code as the whole-ray walk and
+// parks each chunk's sums in shared memory; the ray's first lane then adds all
+// chunk sums in chunk order and finishes the ray.  Every arithmetic step is the
+// whole-ray walk's, in the same order, so the results are the same bits.
+// ---------------------------------------------------------------------------
+constexpr int kSplitMaxChunks = 32;  // rays with more chunks are not split (longer than ~1950 segments)
+
+// Exact walk state after c crossings in the walk's order (by exact position,
+// ties to the lower slot, which is the order every chunk of the whole-ray walk
+// takes: its tie test sends any chunk whose FP32 order could differ to the
+// exact re-walk).  The crossings of each slot before a position X are counted
+// from the arithmetic sequence (Eq. 3) by one 64-bit division, X is pulled back
+// until at most c crossings precede it, and the rest are taken exactly.
+template <int DT>
+__device__ __forceinline__ void jac_state_at(const VolumeDev& vd, const RaySetup& r, const JacRay& jr,
+                                             const JacScratch* ws, int c, JacState& s) {
+  const int t = threadIdx.x;
+  unsigned long long A[3], D[3];
+  unsigned int cnt[3];
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    A[sl] = ws->A0[sl][t];
+    D[sl] = ws->D[sl][t];
+    cnt[sl] = static_cast<unsigned int>(max(ws->cnt[sl][t], 0));
+  }
+  unsigned int n[3] = {0u, 0u, 0u};
+  const unsigned int total = static_cast<unsigned int>(r.nseg - 1);
+  unsigned long long X = static_cast<unsigned long long>(static_cast<double>(c) / total * 0.98 * kFixScale);
+  for (int it = 0; it < 16; ++it) {
+    unsigned int sum = 0u;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      n[sl] = (cnt[sl] == 0u || X <= A[sl]) ? 0u
+                                            : static_cast<unsigned int>(min((X - A[sl] - 1ull) / D[sl] + 1ull,
+                                                                            static_cast<unsigned long long>(cnt[sl])));
+      sum += n[sl];
+    }
+    if (sum <= static_cast<unsigned int>(c)) break;
+    X = it < 14 ? X / (sum + 1u) * static_cast<unsigned int>(c) : 0ull;  // the last pass counts from the entry
+  }
+  unsigned long long e[3];
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) e[sl] = n[sl] < cnt[sl] ? fix_at(A[sl], D[sl], n[sl]) : ~0ull;
+  for (unsigned int m = n[0] + n[1] + n[2]; m < static_cast<unsigned int>(c); ++m) {
+    const bool sx = e[0] <= e[1] && e[0] <= e[2];
+    const bool sy = !sx && e[1] <= e[2];
+    if (sx) { ++n[0]; e[0] = n[0] < cnt[0] ? e[0] + D[0] : ~0ull; }
+    else if (sy) { ++n[1]; e[1] = n[1] < cnt[1] ? e[1] + D[1] : ~0ull; }
+    else { ++n[2]; e[2] = n[2] < cnt[2] ? e[2] + D[2] : ~0ull; }
+  }
+  // the last crossing taken: the largest position (ties: the higher slot, taken later)
+  unsigned long long O = 0ull;
+  int last = -1;
+#pragma unroll
+  for (int sl = 0; sl < 3; ++sl) {
+    if (n[sl] > 0u) {
+      const unsigned long long q = fix_at(A[sl], D[sl], n[sl] - 1u);
+      if (last < 0 || q >= O) { O = q; last = sl; }
+    }
+  }
+  s.k0 = n[0];
+  s.k1 = n[1];
+  s.k2 = n[2];
+  s.O = O;
+  s.off = r.off + static_cast<int>(n[0]) * jr.step[0] + static_cast<int>(n[1]) * jr.step[1] +
+          static_cast<int>(n[2]) * jr.step[2];
+  s.v = gather<DT>(vd, s.off);
+  s.vprev = gather<DT>(vd, s.off - pick3(last, jr.step[0], jr.step[1], jr.step[2]));
+  s.p0 = last == 0;
+  s.p1 = last == 1;
+}
+
+// Persistent split kernel (mode kFwdJac): a block of K warps claims one warp
+// tile (8x4 pixels, pose-major) at a time; warp j walks the j-th run of chunks
+// of all 32 rays (so a warp's lanes are neighbouring rays, as in the whole-ray
+// kernel, and share cache lines); then the first warp adds each ray's chunk
+// sums in chunk order and finishes the rays.
+template <int DT, int K>
+__global__ void __launch_bounds__(32 * K) siddon_split_kernel(VolumeDev vd, DetDev det, const PoseGeom* __restrict__ pgs,
+                                                              int B, unsigned int* __restrict__ counter,
+                                                              float* __restrict__ out, float* __restrict__ jac) {
+  __shared__ PoseGeom pg;
+  __shared__ JacScratch ws;  // indexed by threadIdx.x (< 32 K)
+  __shared__ JacState fin[32];
+  __shared__ float gcs[32];
+  __shared__ unsigned int tile_s;
+  extern __shared__ JacChunk split_chunks[];  // [kSplitMaxChunks][32]: chunk k of ray i at k * 32 + i
+  grid_dep_wait();
+  grid_dep_release();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, piece = warp;
+  const int twx = (det.W + kWarpTileW - 1) / kWarpTileW;
+  const int per_pose = twx * ((det.H + kWarpTileH - 1) / kWarpTileH);
+  const unsigned int total = static_cast<unsigned int>(per_pose) * static_cast<unsigned int>(B);
+  const size_t npix = static_cast<size_t>(det.H) * det.W;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) tile_s = atomicAdd(counter, 1u);
+    __syncthreads();  // also: the block is done with the previous tile
+    const unsigned int tile = tile_s;
+    if (tile >= total) break;
+    const int b = static_cast<int>(tile / static_cast<unsigned int>(per_pose));
+    const int tin = static_cast<int>(tile) - b * per_pose;
+    if (b != cur) {
+      const unsigned int* src = reinterpret_cast<const unsigned int*>(pgs + b);
+      unsigned int* dst = reinterpret_cast<unsigned int*>(&pg);
+      for (int i = threadIdx.x; i < static_cast<int>(sizeof(PoseGeom) / 4); i += 32 * K) dst[i] = src[i];
+      cur = b;
+    }
+    __syncthreads();
+    const int ty = tin / twx, tx = tin - ty * twx;
+    const int h = ty * kWarpTileH + lane / kWarpTileW, w = tx * kWarpTileW + lane % kWarpTileW;
+    const bool valid = (w < det.W) && (h < det.H);
+    RaySetup r;
+    float e[3];
+    const int rs = valid ? ray_setup<true>(vd, pg, h, w, r, e) : 0;
+    JacRay jr;
+    JacState s{};
+    int nch = 0;
+    if (rs > 0) {
+      jac_prepare(r, &ws, jr);
+      const int ncross = r.nseg - 1;
+      nch = (ncross + jr.chunk - 1) / jr.chunk;  // at most kSplitMaxChunks (checked on the host)
+      const int cb = nch * piece / K, ce = nch * (piece + 1) / K;
+      if (cb == 0) {  // the first run, or no crossing at all: from the entry
+        jac_start<DT>(vd, r, jr, s);
+        if (piece == 0) gcs[lane] = r.ea < 0 ? -s.v : 0.f;  // entry clamped at alpha 0: weight -V_first
+      } else if (cb < ce) {
+        jac_state_at<DT>(vd, r, jr, &ws, cb * jr.chunk, s);
+      }
+      for (int k = cb; k < ce; ++k) {
+        const int remaining = ncross - k * jr.chunk;
+        const int n = min(remaining, jr.chunk);
+        jac_chunk<DT>(vd, jr, &ws, s, n, remaining > n, split_chunks[k * 32 + lane]);
+      }
+      // the final state: the last run's (piece K - 1 walks the ray's last
+      // chunk), or piece 0's when the ray has no crossing
+      if (piece == (nch > 0 ? K - 1 : 0)) fin[lane] = s;
+    }
+    __syncthreads();
+    if (warp == 0 && valid) {
+      const size_t pix = static_cast<size_t>(h) * det.W + w;
+      float F = 0.f, J[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (rs < 0) {
+        F = __int_as_float(0x7fffffff);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) J[k] = F;
+      } else if (rs > 0) {
+        JacTotals T{0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < nch; ++k) jac_add_chunk(T, split_chunks[k * 32 + lane]);
+        JacSums js;
+        jac_finish(r, jr, fin[lane], T, gcs[lane], js);
+        const float L = sqrtf(fmaf(r.d[2], r.d[2], fmaf(r.d[1], r.d[1], r.d[0] * r.d[0])));
+        F = js.F * L * vd.out_scale;
+        pose_jacobian(r, js, pg, e, h, w, vd.out_scale, J);
+      }
+      out[b * npix + pix] = F;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) jac[(static_cast<size_t>(b) * 6 + k) * npix + pix] = J[k];
+    }
+  }
+}
+
 // Pose gradient from a stored Jacobian in one launch (Sec. 2.4, chain rule:
 // dL/d eta = sum over pixels of dL/dE * dE/d eta).  One thread-block cluster
 // per pose: block r of the cluster sums g * J over the r-th of kJacCluster
@@ -1592,11 +1836,12 @@ __global__ void __launch_bounds__(kFinThreads) serve_finalize_kernel(const Serve
 #define DRR_PDL 1
 #endif
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream, Args... args) {
+cudaError_t launch_pdl_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                            Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1604,6 +1849,11 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStre
   cfg.attrs = attr;
   cfg.numAttrs = DRR_PDL ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream, Args... args) {
+  return launch_pdl_smem(kernel, grid, block, 0, stream, args...);
 }
 
 int grid_for(int64_t n, int threads) {
@@ -1628,10 +1878,67 @@ int resident_blocks() {
   return cache[dev];
 }
 
+// The split kernel with K warps per tile: its dynamic shared memory (the chunk
+// sums of one tile's rays) and the blocks of it the device holds at once
+// (cached per device; 0 if it cannot be configured).
+constexpr size_t kSplitSmem = static_cast<size_t>(kSplitMaxChunks) * 32 * sizeof(JacChunk);
+template <int DT, int K>
+int split_resident_blocks() {
+  constexpr int kMaxDev = 64;
+  static int cache[kMaxDev] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
+  if (cache[dev] == 0) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(siddon_split_kernel<DT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSplitSmem)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, siddon_split_kernel<DT, K>, 32 * K, kSplitSmem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      cache[dev] = -1;
+    } else {
+      cache[dev] = per_sm > 0 ? sms * per_sm : -1;
+    }
+  }
+  return cache[dev] > 0 ? cache[dev] : 0;
+}
+
+template <int DT, int K>
+cudaError_t launch_split(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, unsigned int* counter,
+                         float* out, float* jac, cudaStream_t stream) {
+  const int64_t tiles = static_cast<int64_t>(pose_tiles(det)) * B;
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, split_resident_blocks<DT, K>()));
+  return launch_pdl_smem(siddon_split_kernel<DT, K>, dim3(grid), dim3(32 * K), kSplitSmem, stream, vd, det, pg, B,
+                         counter, out, jac);
+}
+
+// Warps per ray (per warp tile) for a fused forward + Jacobian launch: 8 or 4
+// when the split kernel's resident blocks can take every tile of the launch at
+// once (the whole-ray walk would leave most of the GPU idle, latency-bound on
+// few warps), 1 otherwise.  Rays are split only where every ray fits the split
+// kernel's chunk table (nx + ny + nz <= 61 * kSplitMaxChunks).
+#ifndef DRR_SPLIT
+#define DRR_SPLIT 1
+#endif
+template <int DT>
+int split_lanes(const VolumeDev& vd, const DetDev& det, int B) {
+  if (!DRR_SPLIT) return 1;
+  if (static_cast<int64_t>(vd.n[0]) + vd.n[1] + vd.n[2] > static_cast<int64_t>(DRR_JAC_LONG) * kSplitMaxChunks) return 1;
+  const int64_t tiles = static_cast<int64_t>(pose_tiles(det)) * B;
+  if (tiles <= split_resident_blocks<DT, 8>()) return 8;
+  if (tiles <= split_resident_blocks<DT, 4>()) return 4;
+  return 1;
+}
+
 template <int MODE, int DT>
 cudaError_t launch_siddon_dt(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, unsigned int* counter,
                              float* out, float* jac, const float* gin, float* partials, float* gvol,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, int lanes = 1) {
+  if (MODE == kFwdJac) {
+    if (lanes == 8) return launch_split<DT, 8>(vd, det, pg, B, counter, out, jac, stream);
+    if (lanes == 4) return launch_split<DT, 4>(vd, det, pg, B, counter, out, jac, stream);
+  }
   const int64_t tiles = static_cast<int64_t>(pose_tiles(det)) * B;
   const int64_t want = (tiles + kThreads / 32 - 1) / (kThreads / 32);
   const int grid = static_cast<int>(std::min<int64_t>(want, resident_blocks<MODE, DT>()));
@@ -1641,14 +1948,17 @@ cudaError_t launch_siddon_dt(const VolumeDev& vd, const DetDev& det, const PoseG
 
 template <int MODE>
 cudaError_t launch_siddon(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
-                          const float* gin, float* partials, float* gvol, cudaStream_t stream) {
+                          const float* gin, float* partials, float* gvol, cudaStream_t stream, int lanes = 1) {
   // one counter per walk kind, so a geometry can serve one launch of each
   const int slot = MODE == kPoseGrad ? 1 : (MODE == kBackproject ? 2 : (MODE == kGeoGrad ? 3 : 0));
   unsigned int* counter = reinterpret_cast<unsigned int*>(const_cast<PoseGeom*>(pg) + B) + slot;
   switch (vd.dtype) {
-    case kF32: return launch_siddon_dt<MODE, kF32>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream);
-    case kBF16: return launch_siddon_dt<MODE, kBF16>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream);
-    default: return launch_siddon_dt<MODE, kF16>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream);
+    case kF32:
+      return launch_siddon_dt<MODE, kF32>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream, lanes);
+    case kBF16:
+      return launch_siddon_dt<MODE, kBF16>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream, lanes);
+    default:
+      return launch_siddon_dt<MODE, kF16>(vd, det, pg, B, counter, out, jac, gin, partials, gvol, stream, lanes);
   }
 }
 
@@ -1793,9 +2103,17 @@ cudaError_t launch_ray_setup(const float* poses, int B, const DetDev& det, float
   return cudaGetLastError();
 }
 
+int render_split_lanes(const VolumeDev& vd, const DetDev& det, int B) {
+  switch (vd.dtype) {
+    case kF32: return split_lanes<kF32>(vd, det, B);
+    case kBF16: return split_lanes<kBF16>(vd, det, B);
+    default: return split_lanes<kF16>(vd, det, B);
+  }
+}
+
 cudaError_t launch_render(const VolumeDev& vd, const DetDev& det, const PoseGeom* pg, int B, float* out, float* jac,
-                          cudaStream_t stream) {
-  if (jac) return launch_siddon<kFwdJac>(vd, det, pg, B, out, jac, nullptr, nullptr, nullptr, stream);
+                          cudaStream_t stream, int lanes) {
+  if (jac) return launch_siddon<kFwdJac>(vd, det, pg, B, out, jac, nullptr, nullptr, nullptr, stream, lanes);
   return launch_siddon<kFwd>(vd, det, pg, B, out, nullptr, nullptr, nullptr, nullptr, stream);
 }
 

@@ -576,8 +576,13 @@ drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* tic
     delete q;
     return drr::set_error(DRR_ERR_INVALID, "the comparison server renders at most 65535 poses per request");
   }
-  q->work = int64_t(req->B) * int64_t(q->npix) * (int64_t(v->vd.n[0]) + v->vd.n[1] + v->vd.n[2]);
-  if (q->grad) q->work += q->work / 2;
+  {
+    // B * H * W * (nx + ny + nz), x 3/2 with a gradient, saturated at 2^62 (the factors
+    // are each below 2^32, so their product can exceed int64)
+    const double w = double(req->B) * double(q->npix) * (double(v->vd.n[0]) + v->vd.n[1] + v->vd.n[2]) *
+                     (q->grad ? 1.5 : 1.0);
+    q->work = w < 4.6e18 ? static_cast<int64_t>(w) : (int64_t{1} << 62);
+  }
   size_request(*q, s->cfg.plain_fp32_baseline != 0);
   if (q->dev_bytes > s->cfg.device_budget_bytes || q->host_bytes > s->cfg.host_budget_bytes) {
     size_t need = q->dev_bytes;
