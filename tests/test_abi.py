@@ -108,3 +108,15 @@ def test_calls_on_a_null_volume_fail_cleanly(lib):
     lib.drr_last_error.restype = ctypes.c_char_p
     st = lib.drr_render(None, None, None, 1, None, None, None)
     assert st == 1 and b"NULL" in lib.drr_last_error()
+
+
+def test_server_configs_are_checked_before_any_device_work(lib):
+    from paper_2208_12737_gb300 import drr
+    lib = drr.load()
+    out = ctypes.c_void_p()
+    for field, value in (("tick_depth", 5), ("tick_depth", 1), ("max_tick_work", -1), ("max_inflight", 5000),
+                         ("max_tick_poses", (1 << 20) + 1)):
+        cfg = drr.drr_server_config()
+        setattr(cfg, field, value)
+        assert lib.drr_server_create(ctypes.byref(cfg), ctypes.byref(out)) == 1, field
+        assert out.value is None
