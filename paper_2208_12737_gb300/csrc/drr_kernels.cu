@@ -1509,8 +1509,14 @@ __global__ void __launch_bounds__(32 * K) siddon_split_kernel(VolumeDev vd, DetD
 // through the cluster's distributed shared memory, and block 0 adds the rows
 // in rank order in FP64.  Every sum has a fixed order, so the result is
 // bitwise reproducible, and no partial sums leave the chip.
-constexpr int kJacCluster = 8;     // blocks per pose (the portable cluster size)
-constexpr int kJacThreads = 1024;  // enough loads in flight per SM for an HBM-rate pass
+constexpr int kJacCluster = 8;  // blocks per pose (the portable cluster size)
+#ifndef DRR_JAC_THREADS
+#define DRR_JAC_THREADS 512
+#endif
+// Threads per block: two 512-thread blocks share an SM, so a cluster spans 4
+// SMs and ~38 clusters run at once (1024-thread blocks allowed 15 at once: a
+// 16-pose batch took two waves, 16.8 us).
+constexpr int kJacThreads = DRR_JAC_THREADS;
 
 __device__ __forceinline__ void jac_fma4(float c[6], const float4 gv, const float* __restrict__ jb, int npix, int i) {
 #pragma unroll
@@ -1526,7 +1532,7 @@ __device__ __forceinline__ void jac_fma4(float c[6], const float4 gv, const floa
 __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(kJacThreads)
     jac_grad_kernel(const float* __restrict__ gin, const float* __restrict__ jac, int npix, int vec,
                     float* __restrict__ grad) {
-  static_assert(kJacThreads == 32 * 32, "the block sum takes one warp sum per lane");
+  static_assert(kJacThreads % 32 == 0 && kJacThreads <= 32 * 32, "the block sum takes one warp sum per lane");
   __shared__ float wsum[kJacThreads / 32][6];
   __shared__ double rows[kJacCluster][6];  // filled in block 0 only
   namespace cg = cooperative_groups;
@@ -1573,7 +1579,7 @@ __global__ void __cluster_dims__(kJacCluster, 1, 1) __launch_bounds__(kJacThread
     float t[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      t[k] = wsum[lane][k];
+      t[k] = lane < kJacThreads / 32 ? wsum[lane][k] : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
     }

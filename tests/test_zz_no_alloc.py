@@ -73,9 +73,10 @@ def test_stored_jacobian_reduction_against_float64(drr, B, H, W, shift):
     ref = _ref_grad(g, J)
     got = out.cpu().numpy().astype(np.float64)
     # FP32 products summed in FP32 by each thread (n terms at most), then a
-    # 10-level FP32 tree over the block's 1024 threads, FP64 across blocks: the
-    # error is below (n + 11) * 2^-24 * sum |g J| (recursive-summation bound)
-    n_per_thread = -(-(H * W) // (8 * 1024)) + 4
+    # 10-level FP32 tree over the block's 512 threads (two 5-level butterflies),
+    # FP64 across blocks: the error is below (n + 11) * 2^-24 * sum |g J|
+    # (recursive-summation bound)
+    n_per_thread = -(-(H * W) // (8 * 512)) + 4
     scale = (g.double().abs().unsqueeze(1) * J.double().abs()).sum(dim=(2, 3)).cpu().numpy()
     assert np.all(np.abs(got - ref) <= (n_per_thread + 11) * 2.0**-24 * scale + 1e-30)
     # bitwise reproducible
