@@ -47,11 +47,17 @@ def _cases():
            np.array([[0, 0, 0, 0.1, 0.2, 0.3], [np.pi / 2, 0, 0, 0, 0, 0]], np.float32))
 
 
-@pytest.mark.parametrize("case", [c[0] for c in _cases()])
-def test_split_walk_gives_the_one_lane_bits(drr, case):
+    # one voxel: every ray has a single segment (no crossing at all)
+    yield ("one_voxel", lambda: (np.full((1, 1, 1), 0.02, np.float32), (40.0, 40.0, 40.0)),
+           inputs.Detector(200.0, 12, 10, 1.0, 1.0), inputs.random_poses(2, seed=53, max_angle_deg=20))
+
+
+@pytest.mark.parametrize("case,storage", [(c[0], "f32") for c in _cases()] + [("small_ct", "bf16"),
+                                                                             ("coincident", "f16")])
+def test_split_walk_gives_the_one_lane_bits(drr, case, storage):
     name, make, det, poses_np = next(c for c in _cases() if c[0] == case)
     vol_np, sp = make()
-    vol = drr.Volume(vol_np, sp)
+    vol = drr.Volume(vol_np, sp, storage=storage)
     B = poses_np.shape[0]
     res = {}
     for reps in (1, 3, 256):  # 8 lanes, 4 (or 8) lanes, and one lane per ray
@@ -66,5 +72,6 @@ def test_split_walk_gives_the_one_lane_bits(drr, case):
     for reps in (1, 3):
         np.testing.assert_array_equal(res[reps][0], res[256][0])
         np.testing.assert_array_equal(res[reps][1], res[256][1])
-    E_ref = oracle.render(ovol(vol_np, sp), odet(det), poses_np)
-    assert rel_err(res[1][0], E_ref).max() < FP32_TOL
+    if storage == "f32":
+        E_ref = oracle.render(ovol(vol_np, sp), odet(det), poses_np)
+        assert rel_err(res[1][0], E_ref).max() < FP32_TOL
