@@ -336,7 +336,9 @@ drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* tic
  * DRR_ERR_DEVICE: a serving kernel found the request's part of the tick table
  * inconsistent (a decoded pose index outside the request) and set the
  * request's device status word instead of touching memory; its outputs were
- * not written.  Several threads may wait at once (on different tickets). */
+ * not written.  Several threads may wait at once, also on one ticket: each
+ * that is waiting when the request finishes gets its result, and the last of
+ * them releases the ticket. */
 drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, drr_result* res);
 
 /* State of a ticket without waiting (no counterpart in the paper). */

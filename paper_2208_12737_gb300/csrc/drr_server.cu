@@ -71,6 +71,7 @@ struct Req {
   drr_status status = DRR_OK;
   unsigned int device_status = 0;  // the tick's status word for this request, after the tick
   unsigned int inject_status = 0;  // host-side fault injection: uploaded as the initial status word
+  int waiters = 0;                 // threads inside drr_server_wait on this ticket (the last one frees it)
 };
 
 struct Tick {
@@ -616,12 +617,14 @@ drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, dr
   Req* q = it->second;
   auto ready = [q] { return q->state == kDone; };
   ++s->waiters;  // drr_server_destroy frees nothing while a waiter is inside
+  ++q->waiters;  // nor does another waiter on the same ticket
   bool finished = true;
   if (timeout_ms < 0) {
     s->cv_done.wait(lk, ready);
   } else {
     finished = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
   }
+  --q->waiters;
   if (--s->waiters == 0) s->cv_done.notify_all();
   if (!finished)
     return drr::set_error(DRR_ERR_TIMEOUT, "ticket %llu not finished after %d ms", (unsigned long long)ticket,
@@ -634,8 +637,12 @@ drr_status drr_server_wait(drr_server s, uint64_t ticket, int32_t timeout_ms, dr
   }
   drr_status st = q->status;
   const unsigned int dev_bits = q->device_status;
-  s->reqs.erase(it);
-  delete q;
+  // the ticket is released by the last thread that waited on it (every waiter
+  // that was inside when the request finished gets its result)
+  if (q->waiters == 0) {
+    s->reqs.erase(ticket);
+    delete q;
+  }
   if (st == DRR_ERR_DEVICE)
     return drr::set_error(st, "request %llu: a serving kernel set its status word (bits 0x%x); outputs not written",
                           (unsigned long long)ticket, dev_bits);

@@ -289,6 +289,42 @@ def test_destroy_while_threads_wait(drr, vols):
     assert sorted(codes) == [8] * 6  # all were queued (paused): cancelled
 
 
+def test_two_threads_wait_on_one_ticket(drr, vols):
+    # both waiters get the request's result; the ticket is released once, by
+    # the last of them, and a later wait finds it gone
+    import threading
+    import time
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 40, 40, 1.5, 1.5)
+    srv = drr.Server(device_budget=64 << 20)
+    srv.pause(True)
+    t = srv.submit(vol, det, inputs.random_poses(2, seed=430))
+    codes = []
+
+    def waiter():
+        try:
+            t.wait(-1)
+            codes.append(0)
+        except drr.DrrError as e:
+            codes.append(e.status)
+
+    threads = [threading.Thread(target=waiter) for _ in range(2)]
+    for th in threads:
+        th.start()
+    time.sleep(0.2)
+    srv.pause(False)
+    for th in threads:
+        th.join(timeout=30)
+        assert not th.is_alive()
+    assert codes == [0, 0]
+    ref, _ = _direct(drr, vol, det, inputs.random_poses(2, seed=430))
+    assert np.array_equal(t.out, ref)
+    with pytest.raises(drr.DrrError) as ei:
+        t.wait(0)
+    assert ei.value.status == 6  # DRR_ERR_NOT_FOUND: released
+    srv.close()
+
+
 def test_tick_work_cap_bounds_each_tick(drr, vols):
     # a cap of about two requests' work per tick: a backlog of equal requests goes
     # into ticks of at most two, a request larger than the cap alone, and every
