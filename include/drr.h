@@ -321,7 +321,8 @@ typedef struct {
   int64_t submitted, completed, failed, cancelled, ticks;
   int32_t pending, inflight;
   size_t device_in_use, device_budget;
-  double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed requests */
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed requests (p50/p99 over
+                                          * the last 2^20 of them, mean and max over all) */
   double gpu_busy_ms;                     /* summed device time of the ticks */
 } drr_server_stats;
 

@@ -157,7 +157,25 @@ struct drr_server_s {
   std::deque<Req*> pending;
   std::unordered_map<uint64_t, Req*> reqs;
   std::deque<Tick*> inflight;
+  // latencies of completed requests: the last kLatencyWindow for the
+  // percentiles (a server that runs for days keeps a bounded record), and the
+  // count, sum and maximum of all of them
+  static constexpr size_t kLatencyWindow = size_t(1) << 20;
   std::vector<double> latencies;
+  size_t lat_next = 0;
+  int64_t lat_count = 0;
+  double lat_sum = 0.0, lat_max = 0.0;
+  void record_latency(double ms) {
+    if (latencies.size() < kLatencyWindow) {
+      latencies.push_back(ms);
+    } else {
+      latencies[lat_next] = ms;
+      lat_next = (lat_next + 1) % kLatencyWindow;
+    }
+    ++lat_count;
+    lat_sum += ms;
+    lat_max = std::max(lat_max, ms);
+  }
   int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, ticks = 0;
   double gpu_busy_ms = 0.0;
   int admitted = 0;
@@ -433,7 +451,7 @@ void drr_server_s::finish_tick(Tick* t) {
     if (q->has_host) host_arena->release(q->host_off);
     q->has_dev = q->has_host = false;
     q->t_done = Clock::now();
-    if (q->status == DRR_OK) latencies.push_back(ms_between(q->t_submit, q->t_done));
+    if (q->status == DRR_OK) record_latency(ms_between(q->t_submit, q->t_done));
     q->state = kDone;
     q->r.volume->refs.fetch_sub(1);
     --admitted;
@@ -710,10 +728,8 @@ drr_status drr_server_get_stats(drr_server s, drr_server_stats* out) {
     };
     out->p50_ms = pct(0.50);
     out->p99_ms = pct(0.99);
-    out->max_ms = v.back();
-    double sum = 0.0;
-    for (double x : v) sum += x;
-    out->mean_ms = sum / v.size();
+    out->max_ms = s->lat_max;
+    out->mean_ms = s->lat_sum / static_cast<double>(s->lat_count);
   }
   return DRR_OK;
 }
