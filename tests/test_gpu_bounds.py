@@ -1,7 +1,7 @@
 """The zero padding of the volume keeps every voxel gather of the walks in
 bounds, and every live back-projection add lands inside the gradient volume:
-the forward, Jacobian and back-projection parity tests run again, in a child
-process, against the bounds-checked build of the library (every gather and add
+the forward, Jacobian, back-projection, split-walk and serving tests run again,
+in a child process, against the bounds-checked build of the library (every gather and add
 checked, a failed check recorded in a device fault word that drr_stream_check
 reports), which must report no failure."""
 import os
@@ -20,7 +20,8 @@ def test_parity_workloads_stay_in_bounds():
     lib = build.build(checked=True)
     env = dict(os.environ, DRR_LIBRARY=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "gpu", "-p", "no:cacheprovider",
-                        "tests/test_gpu_render.py", "tests/test_gpu_grad.py", "tests/test_gpu_limits.py"],
+                        "tests/test_gpu_render.py", "tests/test_gpu_grad.py", "tests/test_gpu_limits.py",
+                        "tests/test_gpu_split.py", "tests/test_gpu_server.py"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     assert " passed" in r.stdout
