@@ -68,3 +68,37 @@ def test_registration_recovers_poses(drr):
     assert np.all(first[conv] >= 0)
     err = (poses - truth)[conv]
     assert np.abs(err[:, :3]).max() < np.deg2rad(0.5) and np.abs(err[:, 3:]).max() < 1.0, err
+
+
+def test_registration_step_gradient_full_size(drr):
+    # the registration workload at its full sizes (512x512x133 CT, 256x256 detector,
+    # 64 problems): the loss and the pose gradient of one step, as the loop composes
+    # them (fused forward + Jacobian, ZNCC and its gradient, the reduction), for two
+    # of the 64 problems at the initial poses and after 10 Adam steps, against the
+    # oracle's render, ZNCC gradient and pose gradient of the same definitions (the
+    # oracle renders its own fixed images)
+    from tests._parity import GRAD_TOL, grad_err, odet, ovol
+    cfg = inputs.REGISTRATION
+    hu = inputs.ct_volume_hu()
+    vol = drr.Volume(hu, cfg["spacing"], hu=True)
+    det = cfg["detector"]
+    B = cfg["batch"]
+    truth = inputs.random_poses(B, seed=cfg["truth_seed"])
+    init = truth + inputs.pose_offsets(B, seed=cfg["offset_seed"])
+    fixed = drr.render(vol, det, torch.from_numpy(truth).cuda())
+    after, _, _ = drr.register(vol, det, fixed, torch.from_numpy(init).cuda(), steps=10)
+    ov = ovol(oracle.hu_to_mu(hu, inputs.MU_WATER).astype(np.float32), cfg["spacing"])
+    picks = (0, 37)
+    fixed_ref = oracle.render(ov, odet(det), truth[list(picks)])
+    for poses_np in (init.astype(np.float32), after.astype(np.float32)):
+        poses = torch.from_numpy(poses_np).cuda()
+        E, J = drr.render(vol, det, poses, jacobian=True)
+        loss, g = drr.zncc(E, fixed, eps=1e-8)
+        G = drr.render_backward(vol, det, poses, g, jac=J).cpu().numpy()
+        sub = poses_np[list(picks)]
+        E_ref = oracle.render(ov, odet(det), sub)
+        L_ref = oracle.zncc_loss(E_ref, fixed_ref, 1e-8)
+        gE = oracle.zncc_loss_grad(E_ref, fixed_ref, 1e-8)
+        G_ref = oracle.pose_grad(ov, odet(det), sub, gE)
+        np.testing.assert_allclose(loss.cpu().numpy()[list(picks)], L_ref, atol=1e-5)
+        assert grad_err(G[list(picks)], G_ref).max() < GRAD_TOL
