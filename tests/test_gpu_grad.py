@@ -177,6 +177,37 @@ def test_central_fd_on_gpu_matches_oracle_fd(drr):
         assert np.abs(fd_gpu[grp] - fd_ref[grp]).max() < 1e-3 * np.abs(fd_ref[grp]).max(), (fd_gpu, fd_ref)
 
 
+def test_ct_full_size_central_fd(drr):
+    # the benchmarked workload (512x512x133, 200x200, 16 poses): central differences of
+    # g . E for every pose and parameter, GPU forward against the oracle's forward under the
+    # same perturbations, per pose and parameter group.  Steps: 1e-3 rad, which moves the
+    # volume's points by 0.1-0.5 mm at this geometry, and 0.1 mm, the same displacement
+    # scale for the translations (at 1e-2 mm the difference of two FP32 DRRs is only ~100x
+    # their rounding, and the translation group's FD differs by up to 3e-3 on that noise)
+    cfg = inputs.CT
+    hu = inputs.ct_volume_hu()
+    det = cfg["detector"]
+    B = cfg["batch"]
+    p0 = inputs.random_poses(B, seed=cfg["pose_seed"]).astype(np.float64)
+    vol = drr.Volume(hu, cfg["spacing"], hu=True)
+    ov = ovol(oracle.hu_to_mu(hu, inputs.MU_WATER).astype(np.float32), cfg["spacing"])
+    g_np = inputs.upstream_grad((B, det.height, det.width), seed=59).astype(np.float64)
+    fd_gpu, fd_ref = np.zeros((B, 6)), np.zeros((B, 6))
+    for k in range(6):
+        h = 1e-3 if k < 3 else 1e-1
+        pp, pm = p0.copy(), p0.copy()
+        pp[:, k] += h
+        pm[:, k] -= h
+        pp, pm = pp.astype(np.float32), pm.astype(np.float32)
+        den = pp[:, k].astype(np.float64) - pm[:, k].astype(np.float64)
+        Ep = drr.render(vol, det, torch.from_numpy(pp).cuda()).cpu().numpy().astype(np.float64)
+        Em = drr.render(vol, det, torch.from_numpy(pm).cuda()).cpu().numpy().astype(np.float64)
+        fd_gpu[:, k] = np.sum(g_np * (Ep - Em), axis=(1, 2)) / den
+        dref = oracle.render(ov, odet(det), pp) - oracle.render(ov, odet(det), pm)
+        fd_ref[:, k] = np.sum(g_np * dref, axis=(1, 2)) / den
+    assert grad_err(fd_gpu, fd_ref).max() < 1e-3, grad_err(fd_gpu, fd_ref)
+
+
 def test_backprojection_adjoint_identity(drr):
     # <g, A V> = <A^T g, V> between the GPU forward and the GPU back-projection
     mu, sp, det, poses_np = _case_small_ct()
