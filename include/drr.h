@@ -132,6 +132,16 @@ drr_status drr_volume_info(drr_volume v, int32_t dims[3], float spacing[3], drr_
 
 /* ---- rendering (Eq. 2 for every detector pixel, Sec. 2.3) ---------------- */
 
+/* Buffers of drr_render, drr_render_plain_fp32 and drr_render_backward ("_dev" arguments) are
+ * checked before any launch: each must be device memory of the volume's
+ * device (the current device) or, except grad_volume_dev, page-locked host
+ * memory mapped for that device (cudaHostAlloc / cudaHostRegister, or a
+ * pinned torch tensor).  The kernels read and write host buffers in place
+ * across the host link, so a caller whose poses live on the host and who
+ * wants E on the host needs no staging copies.  Anything else (pageable host
+ * memory, another device's memory) is DRR_ERR_INVALID.  The caller keeps
+ * ownership; host buffers must stay valid until the stream work is done. */
+
 /* Forward DRR for B poses.
  *  poses_dev   : [B][6] float32 (rz, ry, rx radians; tx, ty, tz mm).
  *  drr_out_dev : [B][H][W] float32, overwritten with E.

@@ -104,6 +104,47 @@ drr_status check_volume(drr_volume v) {
   return DRR_OK;
 }
 
+// The address under which the kernels may access the buffer p of a call on
+// the volume's device: device (or managed) memory of that device as it is, or,
+// where host_ok, page-locked host memory mapped into the device's address
+// space (the kernels then read or write it across the host link, and no
+// staging copy is needed; under unified addressing the address is p itself).
+// Anything else -- pageable host memory, another device's memory -- is
+// DRR_ERR_INVALID here, before a kernel could fault on it.
+drr_status device_view(const void* p, int dev, bool host_ok, const char* what, const void** out) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev)
+    return drr::set_error(DRR_ERR_INVALID, "%s: the current device (%d) is not the volume's (%d)", what, cur, dev);
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return drr::set_error(DRR_ERR_INVALID, "%s: not an address CUDA knows (%s)", what, cudaGetErrorString(e));
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+      return drr::set_error(DRR_ERR_INVALID, "%s is on device %d, the volume on device %d", what, a.device, dev);
+    *out = p;
+    return DRR_OK;
+  }
+  if (a.type == cudaMemoryTypeHost) {
+    if (!host_ok) return drr::set_error(DRR_ERR_INVALID, "%s must be device memory", what);
+    if (!a.devicePointer)
+      return drr::set_error(DRR_ERR_INVALID, "%s: page-locked host memory not mapped for device %d", what, dev);
+    *out = a.devicePointer;
+    return DRR_OK;
+  }
+  return drr::set_error(DRR_ERR_INVALID, "%s: pageable host memory (pin it, or copy it to the device)", what);
+}
+
+template <typename T>
+drr_status device_view(T* p, int dev, bool host_ok, const char* what, T** out) {
+  const void* q = nullptr;
+  if (drr_status s = device_view(static_cast<const void*>(p), dev, host_ok, what, &q)) return s;
+  *out = static_cast<T*>(const_cast<void*>(q));
+  return DRR_OK;
+}
+
 template <typename T>
 struct AsyncBuf {
   T* p = nullptr;
@@ -411,6 +452,11 @@ drr_status drr_render(drr_volume v, const drr_detector* det, const float* poses_
   if (B <= 0) return drr::set_error(DRR_ERR_INVALID, "B must be positive");
   if (B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be <= 65535");
   if (!poses_dev || !drr_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  if (drr_status s = device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = device_view(drr_out_dev, v->device, true, "drr_out", &drr_out_dev)) return s;
+  if (jac_out_dev) {
+    if (drr_status s = device_view(jac_out_dev, v->device, true, "jac_out", &jac_out_dev)) return s;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -433,6 +479,17 @@ drr_status drr_render_backward(drr_volume v, const drr_detector* det, const floa
   if (!poses_dev || !grad_drr_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   if (!grad_pose_dev && !grad_volume_dev)
     return drr::set_error(DRR_ERR_INVALID, "nothing to compute: grad_pose_dev and grad_volume_dev are both NULL");
+  if (drr_status s = device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = device_view(grad_drr_dev, v->device, true, "grad_drr", &grad_drr_dev)) return s;
+  if (jac_dev) {
+    if (drr_status s = device_view(jac_dev, v->device, true, "jac", &jac_dev)) return s;
+  }
+  if (grad_pose_dev) {
+    if (drr_status s = device_view(grad_pose_dev, v->device, true, "grad_pose", &grad_pose_dev)) return s;
+  }
+  if (grad_volume_dev) {  // atomics into host memory would cross the host link per add: device memory only
+    if (drr_status s = device_view(grad_volume_dev, v->device, false, "grad_volume", &grad_volume_dev)) return s;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -487,6 +544,8 @@ drr_status drr_render_plain_fp32(drr_volume v, const drr_detector* det, const fl
   if (drr_status s = check_geometry(v->vd, dd)) return s;
   if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
   if (!poses_dev || !drr_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  if (drr_status s = device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = device_view(drr_out_dev, v->device, true, "drr_out", &drr_out_dev)) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;

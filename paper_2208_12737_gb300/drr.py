@@ -177,10 +177,12 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev_ptr(t, dtype=None, shape=None, name="tensor"):
+def _dev_ptr(t, dtype=None, shape=None, name="tensor", host_ok=False):
+    """Address of a contiguous tensor the kernels may access: a CUDA tensor, or with
+    host_ok a pinned CPU tensor (read or written in place across the host link)."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name} must be a CUDA torch.Tensor")
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise TypeError(f"{name} must be a CUDA torch.Tensor" + (" or a pinned CPU tensor" if host_ok else ""))
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -257,36 +259,45 @@ class Volume:
 
 
 def render(volume: Volume, det, poses, jacobian: bool = False, out=None, jac=None, stream=None):
-    """E (B, H, W) float32 on the poses' device; with jacobian=True also dE/d eta (B, 6, H, W)."""
+    """E (B, H, W) float32; with jacobian=True also dE/d eta (B, 6, H, W).  poses, out and
+    jac may be CUDA tensors or pinned CPU tensors (the kernels read and write those in
+    place); outputs not given are allocated on the poses' device (the current CUDA device
+    for pinned poses)."""
     import torch
     lib = load()
     d = detector(det)
     B = poses.shape[0]
-    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses", host_ok=True)
+    dev = poses.device if poses.is_cuda else torch.device("cuda", torch.cuda.current_device())
     if out is None:
-        out = torch.empty((B, d.height, d.width), device=poses.device, dtype=torch.float32)
-    op = _dev_ptr(out, torch.float32, (B, d.height, d.width), "out")
+        out = torch.empty((B, d.height, d.width), device=dev, dtype=torch.float32)
+    op = _dev_ptr(out, torch.float32, (B, d.height, d.width), "out", host_ok=True)
     jp = None
     if jacobian:
         if jac is None:
-            jac = torch.empty((B, 6, d.height, d.width), device=poses.device, dtype=torch.float32)
-        jp = _dev_ptr(jac, torch.float32, (B, 6, d.height, d.width), "jac")
+            jac = torch.empty((B, 6, d.height, d.width), device=dev, dtype=torch.float32)
+        jp = _dev_ptr(jac, torch.float32, (B, 6, d.height, d.width), "jac", host_ok=True)
     check(lib.drr_render(volume.handle, ctypes.byref(d), pp, B, op, jp, _stream_ptr(stream)))
     return (out, jac) if jacobian else out
 
 
 def render_backward(volume: Volume, det, poses, grad_drr, jac=None, pose_grad: bool = True, grad_volume=None,
-                    stream=None):
-    """Returns dL/d eta (B, 6) (or None) and accumulates dL/dV into grad_volume if given."""
+                    stream=None, grad_pose_out=None):
+    """Returns dL/d eta (B, 6) (or None) and accumulates dL/dV into grad_volume if given.
+    poses, grad_drr, jac and grad_pose_out (where dL/d eta is written, else a new tensor
+    on the poses' device) may be pinned CPU tensors; grad_volume must be on the device."""
     import torch
     lib = load()
     d = detector(det)
     B = poses.shape[0]
-    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses")
-    gp = _dev_ptr(grad_drr, torch.float32, (B, d.height, d.width), "grad_drr")
-    jp = _dev_ptr(jac, torch.float32, (B, 6, d.height, d.width), "jac") if jac is not None else None
-    gpose = torch.empty((B, 6), device=poses.device, dtype=torch.float32) if pose_grad else None
-    gpp = _dev_ptr(gpose, torch.float32, (B, 6), "grad_pose") if pose_grad else None
+    pp = _dev_ptr(poses, torch.float32, (B, 6), "poses", host_ok=True)
+    gp = _dev_ptr(grad_drr, torch.float32, (B, d.height, d.width), "grad_drr", host_ok=True)
+    jp = _dev_ptr(jac, torch.float32, (B, 6, d.height, d.width), "jac", host_ok=True) if jac is not None else None
+    gpose = None
+    if pose_grad:
+        dev = poses.device if poses.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        gpose = grad_pose_out if grad_pose_out is not None else torch.empty((B, 6), device=dev, dtype=torch.float32)
+    gpp = _dev_ptr(gpose, torch.float32, (B, 6), "grad_pose", host_ok=True) if pose_grad else None
     gvp = _dev_ptr(grad_volume, torch.float32, volume.shape_zyx, "grad_volume") if grad_volume is not None else None
     check(lib.drr_render_backward(volume.handle, ctypes.byref(d), pp, B, gp, jp, gpp, gvp, _stream_ptr(stream)))
     return gpose
