@@ -110,14 +110,29 @@ bool layout_tick(int n, const int32_t* B, const drr::DetDev* det, int32_t* tile_
 // Sizes of a request's device and staging buffers (each piece 256-B aligned).
 // The comparison server stages 13 poses per pose of a gradient request, keeps
 // their renders and the FD Jacobian, and gives pose setup its counter slot.
+// Where a request's inputs and results live.  With DRR_SERVE_HOST_IO (the
+// default) the kernels read the poses and the upstream gradient from, and write
+// E and dL/d eta to, the request's part of the pinned host arena (mapped into
+// the device's address space), so a tick needs no input or result copies and
+// its requests finish when its kernels do; device memory holds only the pose
+// geometry and the gradient partials (and the comparison server's 13 renders
+// per pose and their Jacobian).  With DRR_SERVE_HOST_IO=0 those buffers are
+// staged in device memory and copied up and down around the kernels.
+#ifndef DRR_SERVE_HOST_IO
+#define DRR_SERVE_HOST_IO 1
+#endif
+constexpr bool kHostIo = DRR_SERVE_HOST_IO != 0;
+
 void size_request(Req& q, bool plain) {
   const size_t B = static_cast<size_t>(q.r.B);
   const size_t nt = static_cast<size_t>(drr::pose_tiles(q.det));  // gradient partials per pose
   const size_t P = static_cast<size_t>(q.nposes);
-  q.dev_bytes = up(P * 6 * 4) + up(B * q.npix * 4) + up((P + (plain ? 1 : 0)) * sizeof(drr::PoseGeom));
+  q.dev_bytes = up((P + (plain ? 1 : 0)) * sizeof(drr::PoseGeom));
+  if (!kHostIo) q.dev_bytes += up(P * 6 * 4) + up(B * q.npix * 4);
   q.host_bytes = up(P * 6 * 4) + up(B * q.npix * 4);
   if (q.grad) {
-    q.dev_bytes += up(B * q.npix * 4) + up(B * nt * 6 * 4) + up(B * 6 * 4);
+    q.dev_bytes += up(B * nt * 6 * 4);
+    if (!kHostIo) q.dev_bytes += up(B * q.npix * 4) + up(B * 6 * 4);
     q.host_bytes += up(B * q.npix * 4) + up(B * 6 * 4);
     if (plain) q.dev_bytes += up(P * q.npix * 4) + up(B * 6 * q.npix * 4);
   }
@@ -135,6 +150,7 @@ struct drr_server_s {
   cudaStream_t d2h = nullptr;     // result copies
   char* dev_base = nullptr;
   char* host_base = nullptr;
+  char* host_dev_base = nullptr;  // the host arena's address on the device (mapped pinned memory)
   drr::OffsetArena* dev_arena = nullptr;
   drr::OffsetArena* host_arena = nullptr;
   struct Set {
@@ -310,21 +326,31 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     char* h = host_base + q->host_off;
     const bool plain = cfg.plain_fp32_baseline != 0;
     const size_t P = static_cast<size_t>(q->nposes);
-    q->d_poses = reinterpret_cast<float*>(d); d += up(P * 6 * 4);
-    q->d_out = reinterpret_cast<float*>(d); d += up(B * q->npix * 4);
+    // a host-arena buffer under its device address (host I/O), or a device buffer carved from d
+    auto io = [&](char* hp, size_t bytes) {
+      if (kHostIo) return reinterpret_cast<float*>(host_dev_base + (hp - host_base));
+      float* dp = reinterpret_cast<float*>(d);
+      d += up(bytes);
+      return dp;
+    };
+    q->h_poses = reinterpret_cast<float*>(h);
+    q->d_poses = io(h, P * 6 * 4);
+    h += up(P * 6 * 4);
+    q->h_out = reinterpret_cast<float*>(h);
+    q->d_out = io(h, B * q->npix * 4);
+    h += up(B * q->npix * 4);
     q->d_geom = reinterpret_cast<drr::PoseGeom*>(d); d += up((P + (plain ? 1 : 0)) * sizeof(drr::PoseGeom));
-    q->h_poses = reinterpret_cast<float*>(h); h += up(P * 6 * 4);
-    q->h_out = reinterpret_cast<float*>(h); h += up(B * q->npix * 4);
     if (q->grad) {
-      q->d_grad = reinterpret_cast<float*>(d); d += up(B * q->npix * 4);
+      q->h_grad = reinterpret_cast<float*>(h);
+      q->d_grad = io(h, B * q->npix * 4);
+      h += up(B * q->npix * 4);
+      q->h_gpose = reinterpret_cast<float*>(h);
+      q->d_gpose = io(h, B * 6 * 4);
       q->d_partials = reinterpret_cast<float*>(d); d += up(B * nt * 6 * 4);
-      q->d_gpose = reinterpret_cast<float*>(d); d += up(B * 6 * 4);
       if (plain) {
         q->d_e13 = reinterpret_cast<float*>(d); d += up(P * q->npix * 4);
         q->d_jac = reinterpret_cast<float*>(d);
       }
-      q->h_grad = reinterpret_cast<float*>(h); h += up(B * q->npix * 4);
-      q->h_gpose = reinterpret_cast<float*>(h);
     }
     if (P == B) {
       std::memcpy(q->h_poses, q->r.poses, B * 6 * 4);
@@ -371,7 +397,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(st.d_table + status_off, h_status, sbytes, cudaMemcpyHostToDevice, h2d);
   for (Req* q : batch) {
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess || kHostIo) break;
     e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->nposes) * 6 * 4, cudaMemcpyHostToDevice, h2d);
     if (e == cudaSuccess && q->grad)
       e = cudaMemcpyAsync(q->d_grad, q->h_grad, size_t(q->r.B) * q->npix * 4, cudaMemcpyHostToDevice, h2d);
@@ -392,7 +418,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_status, st.d_table + status_off, sbytes, cudaMemcpyDeviceToHost, d2h);
   for (Req* q : batch) {
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess || kHostIo) break;
     e = cudaMemcpyAsync(q->h_out, q->d_out, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, d2h);
     if (e == cudaSuccess && q->grad)
       e = cudaMemcpyAsync(q->h_gpose, q->d_gpose, size_t(q->r.B) * 6 * 4, cudaMemcpyDeviceToHost, d2h);
@@ -509,7 +535,9 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_base), cfg.device_budget_bytes);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_base), cfg.host_budget_bytes, 0);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_base), cfg.host_budget_bytes, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->host_dev_base), s->host_base, 0);
   s->status_off = up(sizeof(drr::ServeHeader) + size_t(cfg.max_inflight) * sizeof(drr::ServeRequest));
   s->table_bytes = s->status_off + size_t(cfg.max_inflight) * sizeof(unsigned int);
   s->depth = cfg.tick_depth;

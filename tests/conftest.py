@@ -21,13 +21,16 @@ def golden():
 
 @pytest.fixture(autouse=True)
 def _bounds_checked_library(request):
-    """With DRR_LIBRARY naming the bounds-checked build, every GPU test ends by
-    checking that no kernel's bounds check failed during it."""
+    """With DRR_LIBRARY naming another build of the library, every GPU test ends by
+    checking that no kernel reported a device error during it; with
+    DRR_EXPECT_CHECKED=1 (the bounds-checked run) the build must be the checked one,
+    so that a failed bounds check could not go unseen."""
     yield
     if not os.environ.get("DRR_LIBRARY") or request.node.get_closest_marker("gpu") is None:
         return
     from paper_2208_12737_gb300 import drr
     lib = drr.load()
-    assert lib.drr_bounds_checked() == 1
+    if os.environ.get("DRR_EXPECT_CHECKED") == "1":
+        assert lib.drr_bounds_checked() == 1
     st = lib.drr_stream_check(None)
     assert st == 0, lib.drr_last_error().decode()

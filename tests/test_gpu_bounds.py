@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_parity_workloads_stay_in_bounds():
     from paper_2208_12737_gb300 import build
     lib = build.build(checked=True)
-    env = dict(os.environ, DRR_LIBRARY=lib)
+    env = dict(os.environ, DRR_LIBRARY=lib, DRR_EXPECT_CHECKED="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "gpu", "-p", "no:cacheprovider",
                         "tests/test_gpu_render.py", "tests/test_gpu_grad.py", "tests/test_gpu_limits.py",
                         "tests/test_gpu_split.py", "tests/test_gpu_server.py"],
