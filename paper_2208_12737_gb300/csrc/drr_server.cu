@@ -203,8 +203,8 @@ struct drr_server_s {
 
   void run();
   bool form_tick(std::unique_lock<std::mutex>& lk);
-  void copy_results(Tick* t);
-  void finish_tick(Tick* t);
+  void copy_result(Tick* t, size_t i);
+  void finish_request(Req* q);
   void sync_streams();
   cudaError_t launch_kernels(int set);
   cudaError_t launch_plain(const Req& q, cudaStream_t ks);
@@ -443,46 +443,38 @@ void drr_server_s::sync_streams() {
   cudaStreamSynchronize(d2h);
 }
 
-// Called WITHOUT the lock once the tick's device work and copies are done: the
-// tick is off the in-flight list and its requests are admitted (not done), so
-// no other thread touches them or their callers' buffers meanwhile.
-void drr_server_s::copy_results(Tick* t) {
+// Called WITHOUT the lock once the tick's device work is done: the tick is off
+// the in-flight list and its requests are admitted (not done), so no other
+// thread touches them or their callers' buffers meanwhile.
+void drr_server_s::copy_result(Tick* t, size_t i) {
   const auto* h_status = reinterpret_cast<const unsigned int*>(sets[t->set].h_table + status_off);
-  for (size_t i = 0; i < t->reqs.size(); ++i) {
-    Req* q = t->reqs[i];
-    if (q->status != DRR_OK) continue;
-    q->device_status = h_status[i];
-    if (q->device_status != 0) {  // a kernel flagged this request: its outputs are not trusted
-      q->status = DRR_ERR_DEVICE;
-      continue;
-    }
-    std::memcpy(q->r.drr_out, q->h_out, size_t(q->r.B) * q->npix * 4);
-    if (q->grad) std::memcpy(q->r.grad_pose_out, q->h_gpose, size_t(q->r.B) * 6 * 4);
+  Req* q = t->reqs[i];
+  if (q->status != DRR_OK) return;
+  q->device_status = h_status[i];
+  if (q->device_status != 0) {  // a kernel flagged this request: its outputs are not trusted
+    q->status = DRR_ERR_DEVICE;
+    return;
   }
+  std::memcpy(q->r.drr_out, q->h_out, size_t(q->r.B) * q->npix * 4);
+  if (q->grad) std::memcpy(q->r.grad_pose_out, q->h_gpose, size_t(q->r.B) * 6 * 4);
 }
 
-// Called with the lock held after copy_results.
-void drr_server_s::finish_tick(Tick* t) {
-  if (t->timed) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, sets[t->set].start, sets[t->set].stop) == cudaSuccess) gpu_busy_ms += ms;
+// Called with the lock held after copy_result: the request is done (its
+// waiter wakes) and its memory goes back to the arenas.
+void drr_server_s::finish_request(Req* q) {
+  if (q->status == DRR_OK) {
+    ++completed;
+  } else {
+    ++failed;
   }
-  for (Req* q : t->reqs) {
-    if (q->status == DRR_OK) {
-      ++completed;
-    } else {
-      ++failed;
-    }
-    if (q->has_dev) dev_arena->release(q->dev_off);
-    if (q->has_host) host_arena->release(q->host_off);
-    q->has_dev = q->has_host = false;
-    q->t_done = Clock::now();
-    if (q->status == DRR_OK) record_latency(ms_between(q->t_submit, q->t_done));
-    q->state = kDone;
-    q->r.volume->refs.fetch_sub(1);
-    --admitted;
-  }
-  delete t;
+  if (q->has_dev) dev_arena->release(q->dev_off);
+  if (q->has_host) host_arena->release(q->host_off);
+  q->has_dev = q->has_host = false;
+  q->t_done = Clock::now();
+  if (q->status == DRR_OK) record_latency(ms_between(q->t_submit, q->t_done));
+  q->state = kDone;
+  q->r.volume->refs.fetch_sub(1);
+  --admitted;
   cv_done.notify_all();
 }
 
@@ -493,10 +485,19 @@ void drr_server_s::run() {
     while (!inflight.empty() && inflight.front()->done.load()) {
       Tick* t = inflight.front();
       inflight.pop_front();
-      lk.unlock();
-      copy_results(t);
-      lk.lock();
-      finish_tick(t);
+      if (t->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sets[t->set].start, sets[t->set].stop) == cudaSuccess) gpu_busy_ms += ms;
+      }
+      // each request is done as soon as its own results are in the caller's
+      // buffers, not once the whole tick's are (a tick's copies take ~20 us per MB)
+      for (size_t i = 0; i < t->reqs.size(); ++i) {
+        lk.unlock();
+        copy_result(t, i);
+        lk.lock();
+        finish_request(t->reqs[i]);
+      }
+      delete t;
     }
     if (stop && inflight.empty()) break;
     bool launched = false;
