@@ -132,15 +132,18 @@ drr_status drr_volume_info(drr_volume v, int32_t dims[3], float spacing[3], drr_
 
 /* ---- rendering (Eq. 2 for every detector pixel, Sec. 2.3) ---------------- */
 
-/* Buffers of drr_render, drr_render_plain_fp32 and drr_render_backward ("_dev" arguments) are
- * checked before any launch: each must be device memory of the volume's
- * device (the current device) or, except grad_volume_dev, page-locked host
- * memory mapped for that device (cudaHostAlloc / cudaHostRegister, or a
- * pinned torch tensor).  The kernels read and write host buffers in place
- * across the host link, so a caller whose poses live on the host and who
- * wants E on the host needs no staging copies.  Anything else (pageable host
- * memory, another device's memory) is DRR_ERR_INVALID.  The caller keeps
- * ownership; host buffers must stay valid until the stream work is done. */
+/* Buffers.  Every call that takes buffers for the kernels ("_dev"
+ * arguments, and volume data with data_on_device != 0) checks each one before
+ * any launch: it must be device memory of the current device (the volume's,
+ * for calls on a volume) or page-locked host memory mapped for that device
+ * (cudaHostAlloc / cudaHostRegister, or a pinned torch tensor).  The kernels
+ * read and write host buffers in place across the host link, so a caller whose
+ * poses live on the host and who wants E on the host needs no staging copies.
+ * Two buffers must be device memory: drr_render_backward's grad_volume_dev
+ * (accumulated with atomic adds) and the L2 probe's buffer.  Anything else
+ * (pageable host memory, another device's memory) is DRR_ERR_INVALID, before
+ * a kernel could fault on it.  The caller keeps ownership; host buffers must
+ * stay valid until the stream work is done. */
 
 /* Forward DRR for B poses.
  *  poses_dev   : [B][6] float32 (rz, ry, rx radians; tx, ty, tz mm).

@@ -68,6 +68,46 @@ void configure_pool(int dev) {
   });
 }
 
+// The address under which the kernels may access the buffer p of a call on
+// the volume's device: device (or managed) memory of that device as it is, or,
+// where host_ok, page-locked host memory mapped into the device's address
+// space (the kernels then read or write it across the host link, and no
+// staging copy is needed; under unified addressing the address is p itself).
+// Anything else -- pageable host memory, another device's memory -- is
+// DRR_ERR_INVALID here, before a kernel could fault on it.
+drr_status device_view(const void* p, int dev, bool host_ok, const char* what, const void** out) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev)
+    return set_error(DRR_ERR_INVALID, "%s: the current device (%d) is not the volume's (%d)", what, cur, dev);
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(DRR_ERR_INVALID, "%s: not an address CUDA knows (%s)", what, cudaGetErrorString(e));
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+      return set_error(DRR_ERR_INVALID, "%s is on device %d, the volume on device %d", what, a.device, dev);
+    *out = p;
+    return DRR_OK;
+  }
+  if (a.type == cudaMemoryTypeHost) {
+    if (!host_ok) return set_error(DRR_ERR_INVALID, "%s must be device memory", what);
+    if (!a.devicePointer)
+      return set_error(DRR_ERR_INVALID, "%s: page-locked host memory not mapped for device %d", what, dev);
+    *out = a.devicePointer;
+    return DRR_OK;
+  }
+  return set_error(DRR_ERR_INVALID, "%s: pageable host memory (pin it, or copy it to the device)", what);
+}
+
+
+int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) return -1;
+  return d;
+}
+
 drr_status check_detector(const drr_detector* det, drr::DetDev* out) {
   if (!det) return drr::set_error(DRR_ERR_INVALID, "detector is NULL");
   if (det->height <= 0 || det->width <= 0) return drr::set_error(DRR_ERR_INVALID, "detector size must be positive");
@@ -104,46 +144,6 @@ drr_status check_volume(drr_volume v) {
   return DRR_OK;
 }
 
-// The address under which the kernels may access the buffer p of a call on
-// the volume's device: device (or managed) memory of that device as it is, or,
-// where host_ok, page-locked host memory mapped into the device's address
-// space (the kernels then read or write it across the host link, and no
-// staging copy is needed; under unified addressing the address is p itself).
-// Anything else -- pageable host memory, another device's memory -- is
-// DRR_ERR_INVALID here, before a kernel could fault on it.
-drr_status device_view(const void* p, int dev, bool host_ok, const char* what, const void** out) {
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev)
-    return drr::set_error(DRR_ERR_INVALID, "%s: the current device (%d) is not the volume's (%d)", what, cur, dev);
-  cudaPointerAttributes a{};
-  const cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return drr::set_error(DRR_ERR_INVALID, "%s: not an address CUDA knows (%s)", what, cudaGetErrorString(e));
-  }
-  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
-    if (a.type == cudaMemoryTypeDevice && a.device != dev)
-      return drr::set_error(DRR_ERR_INVALID, "%s is on device %d, the volume on device %d", what, a.device, dev);
-    *out = p;
-    return DRR_OK;
-  }
-  if (a.type == cudaMemoryTypeHost) {
-    if (!host_ok) return drr::set_error(DRR_ERR_INVALID, "%s must be device memory", what);
-    if (!a.devicePointer)
-      return drr::set_error(DRR_ERR_INVALID, "%s: page-locked host memory not mapped for device %d", what, dev);
-    *out = a.devicePointer;
-    return DRR_OK;
-  }
-  return drr::set_error(DRR_ERR_INVALID, "%s: pageable host memory (pin it, or copy it to the device)", what);
-}
-
-template <typename T>
-drr_status device_view(T* p, int dev, bool host_ok, const char* what, T** out) {
-  const void* q = nullptr;
-  if (drr_status s = device_view(static_cast<const void*>(p), dev, host_ok, what, &q)) return s;
-  *out = static_cast<T*>(const_cast<void*>(q));
-  return DRR_OK;
-}
 
 template <typename T>
 struct AsyncBuf {
@@ -319,7 +319,9 @@ drr_status drr_volume_create(const void* data, int32_t data_on_device, drr_dtype
 
   const void* src = data;
   void* staged = nullptr;
-  if (!data_on_device) {
+  if (data_on_device) {
+    if (drr_status s = drr::device_view(data, dev, true, "data", &src)) return s;
+  } else {
     DRR_CUDA(cudaMallocAsync(&staged, src_bytes, st), "cudaMallocAsync(volume staging)");
     cudaError_t e = cudaMemcpyAsync(staged, data, src_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
@@ -437,6 +439,9 @@ drr_status drr_ray_setup(const drr_detector* det, const float* poses_dev, int32_
   if (drr_status s = check_detector(det, &dd)) return s;
   if (B <= 0) return drr::set_error(DRR_ERR_INVALID, "B must be positive");
   if (!poses_dev || !rays_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  const int dev = drr::current_device();
+  if (drr_status s = drr::device_view(poses_dev, dev, true, "poses", &poses_dev)) return s;
+  if (drr_status s = drr::device_view(rays_out_dev, dev, true, "rays_out", &rays_out_dev)) return s;
   LaunchScope ls(kPoseSetup, static_cast<cudaStream_t>(cuda_stream));
   DRR_CUDA(drr::launch_ray_setup(poses_dev, B, dd, rays_out_dev, static_cast<cudaStream_t>(cuda_stream)),
            "ray_setup launch");
@@ -452,10 +457,10 @@ drr_status drr_render(drr_volume v, const drr_detector* det, const float* poses_
   if (B <= 0) return drr::set_error(DRR_ERR_INVALID, "B must be positive");
   if (B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be <= 65535");
   if (!poses_dev || !drr_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
-  if (drr_status s = device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
-  if (drr_status s = device_view(drr_out_dev, v->device, true, "drr_out", &drr_out_dev)) return s;
+  if (drr_status s = drr::device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = drr::device_view(drr_out_dev, v->device, true, "drr_out", &drr_out_dev)) return s;
   if (jac_out_dev) {
-    if (drr_status s = device_view(jac_out_dev, v->device, true, "jac_out", &jac_out_dev)) return s;
+    if (drr_status s = drr::device_view(jac_out_dev, v->device, true, "jac_out", &jac_out_dev)) return s;
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
@@ -479,16 +484,16 @@ drr_status drr_render_backward(drr_volume v, const drr_detector* det, const floa
   if (!poses_dev || !grad_drr_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   if (!grad_pose_dev && !grad_volume_dev)
     return drr::set_error(DRR_ERR_INVALID, "nothing to compute: grad_pose_dev and grad_volume_dev are both NULL");
-  if (drr_status s = device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
-  if (drr_status s = device_view(grad_drr_dev, v->device, true, "grad_drr", &grad_drr_dev)) return s;
+  if (drr_status s = drr::device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = drr::device_view(grad_drr_dev, v->device, true, "grad_drr", &grad_drr_dev)) return s;
   if (jac_dev) {
-    if (drr_status s = device_view(jac_dev, v->device, true, "jac", &jac_dev)) return s;
+    if (drr_status s = drr::device_view(jac_dev, v->device, true, "jac", &jac_dev)) return s;
   }
   if (grad_pose_dev) {
-    if (drr_status s = device_view(grad_pose_dev, v->device, true, "grad_pose", &grad_pose_dev)) return s;
+    if (drr_status s = drr::device_view(grad_pose_dev, v->device, true, "grad_pose", &grad_pose_dev)) return s;
   }
   if (grad_volume_dev) {  // atomics into host memory would cross the host link per add: device memory only
-    if (drr_status s = device_view(grad_volume_dev, v->device, false, "grad_volume", &grad_volume_dev)) return s;
+    if (drr_status s = drr::device_view(grad_volume_dev, v->device, false, "grad_volume", &grad_volume_dev)) return s;
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
@@ -527,6 +532,8 @@ drr_status drr_count_segments(drr_volume v, const drr_detector* det, const float
   if (drr_status s = check_geometry(v->vd, dd)) return s;
   if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
   if (!poses_dev || !segments_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  if (drr_status s = drr::device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = drr::device_view(segments_out_dev, v->device, true, "segments_out", &segments_out_dev)) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -544,8 +551,8 @@ drr_status drr_render_plain_fp32(drr_volume v, const drr_detector* det, const fl
   if (drr_status s = check_geometry(v->vd, dd)) return s;
   if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
   if (!poses_dev || !drr_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
-  if (drr_status s = device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
-  if (drr_status s = device_view(drr_out_dev, v->device, true, "drr_out", &drr_out_dev)) return s;
+  if (drr_status s = drr::device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = drr::device_view(drr_out_dev, v->device, true, "drr_out", &drr_out_dev)) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -563,6 +570,10 @@ drr_status drr_geometry_grad(drr_volume v, const drr_detector* det, const float*
   if (drr_status s = check_geometry(v->vd, dd)) return s;
   if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
   if (!poses_dev || !grad_drr_dev || !grad_geometry_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  if (drr_status s = drr::device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = drr::device_view(grad_drr_dev, v->device, true, "grad_drr", &grad_drr_dev)) return s;
+  if (drr_status s = drr::device_view(grad_geometry_dev, v->device, true, "grad_geometry", &grad_geometry_dev))
+    return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   configure_pool(v->device);
   AsyncBuf<drr::PoseGeom> pg;
@@ -586,6 +597,9 @@ drr_status drr_loss_landscape(drr_volume v, const drr_detector* det, const float
   if (chunk < 0) return drr::set_error(DRR_ERR_INVALID, "chunk must be >= 0");
   if (!(eps >= 0.f)) return drr::set_error(DRR_ERR_INVALID, "eps must be >= 0");
   if (!fixed_dev || !poses_dev || !loss_out_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  if (drr_status s = drr::device_view(fixed_dev, v->device, true, "fixed", &fixed_dev)) return s;
+  if (drr_status s = drr::device_view(poses_dev, v->device, true, "poses", &poses_dev)) return s;
+  if (drr_status s = drr::device_view(loss_out_dev, v->device, true, "loss_out", &loss_out_dev)) return s;
   const int64_t npix = int64_t(dd.H) * dd.W;
   if (chunk == 0) chunk = int32_t(std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t{256} << 20) / (4 * npix))));
   chunk = std::min(chunk, std::min<int32_t>(N, 65535));

@@ -183,6 +183,19 @@ drr_status cuda_error(cudaError_t e, const char* what);
 drr_status check_detector(const drr_detector* det, DetDev* out);
 drr_status check_geometry(const VolumeDev& vd, const DetDev& det);
 void configure_pool(int dev);
+// The address under which the kernels may access buffer p on device dev:
+// device (or managed) memory of dev as it is, or, where host_ok, mapped
+// page-locked host memory; anything else is DRR_ERR_INVALID (drr_api.cu).
+drr_status device_view(const void* p, int dev, bool host_ok, const char* what, const void** out);
+template <typename T>
+drr_status device_view(T* p, int dev, bool host_ok, const char* what, T** out) {
+  const void* q = nullptr;
+  if (drr_status s = device_view(static_cast<const void*>(p), dev, host_ok, what, &q)) return s;
+  *out = static_cast<T*>(const_cast<void*>(q));
+  return DRR_OK;
+}
+// The calling thread's current device (-1 if CUDA cannot say).
+int current_device();
 void count_launches(int n);  // kernel launches issued outside LaunchScope (serving ticks)
 
 }  // namespace drr

@@ -20,6 +20,11 @@ extern "C" drr_status drr_pose_grad_noalloc(const drr_detector* det, int32_t B, 
   if (drr_status s = drr::check_detector(det, &dd)) return s;
   if (B <= 0 || B > 65535) return drr::set_error(DRR_ERR_INVALID, "B must be in [1, 65535]");
   if (!grad_drr_dev || !jac_dev || !grad_pose_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  // (a pointer query, no allocation)
+  const int dev = drr::current_device();
+  if (drr_status s = drr::device_view(grad_drr_dev, dev, true, "grad_drr", &grad_drr_dev)) return s;
+  if (drr_status s = drr::device_view(jac_dev, dev, true, "jac", &jac_dev)) return s;
+  if (drr_status s = drr::device_view(grad_pose_dev, dev, true, "grad_pose", &grad_pose_dev)) return s;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = drr::launch_pose_grad_from_jacobian(dd, B, grad_drr_dev, jac_dev, grad_pose_dev, st);
   if (e != cudaSuccess) return drr::cuda_error(e, "drr_pose_grad_noalloc launch");

@@ -29,8 +29,9 @@ extern "C" drr_status drr_probe_l2_read(const void* buf_dev, size_t bytes, int32
                                         void* cuda_stream) {
   if (!buf_dev || !sink_dev || bytes < 16 || reps <= 0) return drr::set_error(DRR_ERR_INVALID, "bad probe arguments");
   if (reinterpret_cast<uintptr_t>(buf_dev) % 16 != 0) return drr::set_error(DRR_ERR_INVALID, "buffer not 16-byte aligned");
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
+  int dev = drr::current_device(), sms = 0;
+  if (drr_status s = drr::device_view(buf_dev, dev, false, "buf", &buf_dev)) return s;  // an L2 probe: device memory
+  if (drr_status s = drr::device_view(sink_dev, dev, true, "sink", &sink_dev)) return s;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (sms > 0 ? sms : 1) * 8;
   l2_read_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(static_cast<const float4*>(buf_dev),

@@ -108,6 +108,15 @@ extern "C" drr_status drr_zncc(const float* moving_dev, const float* fixed_dev, 
   if (B <= 0 || npix <= 0) return drr::set_error(DRR_ERR_INVALID, "B and npix must be positive");
   if (!moving_dev || !fixed_dev || (!loss_dev && !grad_dev)) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
   if (!(eps >= 0.f)) return drr::set_error(DRR_ERR_INVALID, "eps must be >= 0");
+  const int dev = drr::current_device();
+  if (drr_status s = drr::device_view(moving_dev, dev, true, "moving", &moving_dev)) return s;
+  if (drr_status s = drr::device_view(fixed_dev, dev, true, "fixed", &fixed_dev)) return s;
+  if (loss_dev) {
+    if (drr_status s = drr::device_view(loss_dev, dev, true, "loss", &loss_dev)) return s;
+  }
+  if (grad_dev) {
+    if (drr_status s = drr::device_view(grad_dev, dev, true, "grad", &grad_dev)) return s;
+  }
   cudaError_t e = drr::launch_zncc(moving_dev, fixed_dev, static_cast<size_t>(npix), B, npix, eps, loss_dev, grad_dev,
                                    static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return drr::cuda_error(e, "zncc launch");
@@ -120,6 +129,11 @@ extern "C" drr_status drr_adam_step(float* params_dev, const float* grads_dev, f
                                     void* cuda_stream) {
   if (B <= 0 || step <= 0) return drr::set_error(DRR_ERR_INVALID, "B and step must be positive");
   if (!params_dev || !grads_dev || !m_dev || !v_dev) return drr::set_error(DRR_ERR_INVALID, "NULL pointer");
+  const int dev = drr::current_device();
+  if (drr_status s = drr::device_view(params_dev, dev, true, "params", &params_dev)) return s;
+  if (drr_status s = drr::device_view(grads_dev, dev, true, "grads", &grads_dev)) return s;
+  if (drr_status s = drr::device_view(m_dev, dev, true, "m", &m_dev)) return s;
+  if (drr_status s = drr::device_view(v_dev, dev, true, "v", &v_dev)) return s;
   const int n = 6 * B;
   adam_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
       params_dev, grads_dev, m_dev, v_dev, n, step, lr_rot, lr_trans, beta1, beta2, eps);
