@@ -80,6 +80,14 @@ def test_pageable_and_misplaced_buffers_are_rejected(drr, case):
                                  None, None, ptr(gv_h), stream)
     assert st == 1 and "device memory" in lib.drr_last_error().decode()
     assert np.all(pageable == 0) and float(gv_h.abs().sum()) == 0.0
+    # the other entry points check their buffers the same way
+    st = lib.drr_zncc(ctypes.c_void_p(pageable.ctypes.data), ptr(out_d), 5, 45 * 53, ctypes.c_float(1e-8),
+                      ptr(torch.empty(5, device="cuda")), None, stream)
+    assert st == 1
+    jac_d = torch.zeros((5, 6, 45, 53), device="cuda")
+    st = lib.drr_pose_grad_noalloc(ctypes.byref(d), 5, ctypes.c_void_p(pageable.ctypes.data), ptr(jac_d),
+                                   ptr(torch.empty((5, 6), device="cuda")), stream)
+    assert st == 1
     # the Python binding refuses a CPU tensor that is not pinned
     with pytest.raises(TypeError):
         drr.render(vol, det, torch.from_numpy(poses_np))
