@@ -304,13 +304,19 @@ typedef struct {
                                  ticks can be formed and queued while it runs */
 } drr_server_config;
 
-/* A request carries the upstream gradient dL/dE itself, not a loss kind: a
- * loss of the DRR (e.g. -ZNCC against a fixed image) needs the DRR before its
- * gradient exists, i.e. a second walk in the same tick, while dL/dE supplied
- * by the caller gives the pose gradient in the tick's single walk.  A
- * registration step is served as two requests (render, then render+gradient
- * with dL/dE from drr_zncc), or run directly with drr_render /
- * drr_render_backward. */
+/* A request is one of three kinds:
+ *  - a render: E for each pose;
+ *  - a render with a pose gradient, the upstream gradient dL/dE given
+ *    (grad_drr): E and sum_{h,w} dL/dE dE/d eta per pose, from the tick's one
+ *    packed walk (each tile's g . J summed in the walk);
+ *  - a registration step (Sec. 3.2), fixed images given (fixed): E, the loss
+ *    -ZNCC(E, fixed) per pose (population statistics, as drr_zncc) and its pose
+ *    gradient.  dL/dE exists only once the whole DRR does, so such a request is
+ *    not packed into the tick's walk: the tick runs for it, after the walk, the
+ *    direct calls' launches (the fused forward + Jacobian render, drr_zncc, the
+ *    stored-Jacobian reduction), and its results are the same bits as
+ *    drr_render + drr_zncc + drr_render_backward on the same inputs.
+ * The comparison server (plain_fp32_baseline) takes the first two kinds. */
 typedef struct {
   drr_volume volume;        /* must stay alive until the request completes (destroy returns BUSY) */
   drr_detector detector;
@@ -318,7 +324,11 @@ typedef struct {
   const float* poses;       /* host [B][6] */
   const float* grad_drr;    /* host [B][H][W] dL/dE for a render+gradient request, or NULL */
   float* drr_out;           /* host [B][H][W], written before drr_server_wait returns DRR_OK */
-  float* grad_pose_out;     /* host [B][6], required iff grad_drr != NULL */
+  float* grad_pose_out;     /* host [B][6], required iff grad_drr or fixed is given */
+  const float* fixed;       /* host [B][H][W] fixed images of a registration step, or NULL
+                               (grad_drr must then be NULL) */
+  float* loss_out;          /* host [B] -ZNCC per pose, required iff fixed != NULL */
+  float zncc_eps;           /* the ZNCC's eps (>= 0); 0 -> 1e-8 */
 } drr_request;
 /* All host buffers of a request are caller-owned and must stay valid until
  * drr_server_wait has returned for its ticket. */

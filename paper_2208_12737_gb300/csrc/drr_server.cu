@@ -52,7 +52,8 @@ struct Req {
   uint64_t id = 0;
   drr_request r{};
   drr::DetDev det{};
-  bool grad = false;
+  bool grad = false;  // a pose gradient is wanted (upstream gradient given, or a registration step)
+  bool zncc = false;  // a registration step: fixed images given, the loss -ZNCC and its gradient
   size_t npix = 0;
   int64_t work = 0;  // estimated ray-planes (the tick-work cap's unit)
   int nposes = 0;    // poses rendered: B, or 13 B for a central-difference gradient (comparison server)
@@ -62,9 +63,12 @@ struct Req {
   // device buffers (inside the device arena)
   float *d_poses = nullptr, *d_grad = nullptr, *d_out = nullptr, *d_partials = nullptr, *d_gpose = nullptr;
   float *d_e13 = nullptr, *d_jac = nullptr;  // comparison server: the 13 renders per pose and the FD Jacobian
+  // registration step: E and its Jacobian, the fixed images and dL/dE on the device; the loss
+  float *d_e = nullptr, *d_fixed = nullptr, *d_loss = nullptr;
   drr::PoseGeom* d_geom = nullptr;
   // pinned staging (inside the host arena)
   float *h_poses = nullptr, *h_grad = nullptr, *h_out = nullptr, *h_gpose = nullptr;
+  float *h_fixed = nullptr, *h_loss = nullptr;
   Clock::time_point t_submit, t_admit, t_done;
   int64_t tick = -1;
   ReqState state = kPending;
@@ -127,6 +131,13 @@ void size_request(Req& q, bool plain) {
   const size_t B = static_cast<size_t>(q.r.B);
   const size_t nt = static_cast<size_t>(drr::pose_tiles(q.det));  // gradient partials per pose
   const size_t P = static_cast<size_t>(q.nposes);
+  if (q.zncc) {  // geometry (+ the tile counters), E, its 6 Jacobian planes, dL/dE, the fixed images
+    q.dev_bytes = up((B + 1) * sizeof(drr::PoseGeom)) + up(B * q.npix * 4) + up(6 * B * q.npix * 4) +
+                  up(B * q.npix * 4) + up(B * q.npix * 4);
+    if (!kHostIo) q.dev_bytes += up(B * 6 * 4) + up(B * 6 * 4) + up(B * 4);
+    q.host_bytes = up(B * 6 * 4) + up(B * q.npix * 4) + up(B * q.npix * 4) + up(B * 6 * 4) + up(B * 4);
+    return;
+  }
   q.dev_bytes = up((P + (plain ? 1 : 0)) * sizeof(drr::PoseGeom));
   if (!kHostIo) q.dev_bytes += up(P * 6 * 4) + up(B * q.npix * 4);
   q.host_bytes = up(P * 6 * 4) + up(B * q.npix * 4);
@@ -208,6 +219,7 @@ struct drr_server_s {
   void sync_streams();
   cudaError_t launch_kernels(int set);
   cudaError_t launch_plain(const Req& q, cudaStream_t ks);
+  cudaError_t launch_registration_step(const Req& q, cudaStream_t ks);
 };
 
 namespace {
@@ -245,6 +257,22 @@ cudaError_t drr_server_s::launch_plain(const Req& q, cudaStream_t ks) {
   if (e == cudaSuccess)
     e = drr::launch_plain_fd_finish(q.d_e13, q.r.B, static_cast<int>(q.npix), kFdRot, kFdTrans, q.d_out, q.d_jac, ks);
   if (e == cudaSuccess) e = drr::launch_pose_grad_from_jacobian(q.det, q.r.B, q.d_grad, q.d_jac, q.d_gpose, ks);
+  return e;
+}
+
+// A registration step (Sec. 3.2): the direct calls' launches in their order --
+// pose setup, the fused forward + Jacobian render (the same split-walk choice
+// as drr_render), the ZNCC loss and dL/dE, and the stored-Jacobian pose
+// gradient -- so its results are the direct path's bits.
+cudaError_t drr_server_s::launch_registration_step(const Req& q, cudaStream_t ks) {
+  const drr::VolumeDev& vd = q.r.volume->vd;
+  const int B = q.r.B;
+  cudaError_t e = drr::launch_pose_setup(q.d_poses, B, q.det, &vd, q.d_geom, ks);
+  if (e == cudaSuccess)
+    e = drr::launch_render(vd, q.det, q.d_geom, B, q.d_e, q.d_jac, ks, drr::render_split_lanes(vd, q.det, B));
+  if (e == cudaSuccess)
+    e = drr::launch_zncc(q.d_e, q.d_fixed, q.npix, B, static_cast<int>(q.npix), q.r.zncc_eps, q.d_loss, q.d_grad, ks);
+  if (e == cudaSuccess) e = drr::launch_pose_grad_from_jacobian(q.det, B, q.d_grad, q.d_jac, q.d_gpose, ks);
   return e;
 }
 
@@ -291,6 +319,10 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   }
   if (batch.empty()) return false;
   admitted += static_cast<int>(batch.size());
+  // the packed walk's requests first (table entries 0 .. nw - 1), then the
+  // registration steps, which run their own launches after the walk
+  std::stable_partition(batch.begin(), batch.end(), [](const Req* q) { return !q->zncc; });
+  const int nw = static_cast<int>(std::count_if(batch.begin(), batch.end(), [](const Req* q) { return !q->zncc; }));
   Tick* t = new Tick();
   t->id = next_tick++;
   t->set = static_cast<int>(t->id % depth);
@@ -313,7 +345,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   int32_t total_tiles = 0, total_poses = 0;
   // admission caps the tick at max_tick_poses <= 2^20 poses of < 2^30 tiles each
   // request, so the layout always fits; a failure leaves the tick empty
-  if (!layout_tick(n, Bs.data(), dets.data(), tstart.data(), pstart.data(), &total_tiles, &total_poses)) {
+  if (nw > 0 && !layout_tick(nw, Bs.data(), dets.data(), tstart.data(), pstart.data(), &total_tiles, &total_poses)) {
     total_tiles = total_poses = 0;
     if (e == cudaSuccess) e = cudaErrorInvalidValue;
   }
@@ -333,6 +365,34 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
       d += up(bytes);
       return dp;
     };
+    if (q->zncc) {
+      auto dev = [&](size_t bytes) {
+        float* dp = reinterpret_cast<float*>(d);
+        d += up(bytes);
+        return dp;
+      };
+      q->d_geom = reinterpret_cast<drr::PoseGeom*>(dev((B + 1) * sizeof(drr::PoseGeom)));
+      q->d_e = dev(B * q->npix * 4);
+      q->d_jac = dev(6 * B * q->npix * 4);
+      q->d_grad = dev(B * q->npix * 4);
+      q->d_fixed = dev(B * q->npix * 4);
+      q->h_poses = reinterpret_cast<float*>(h);
+      q->d_poses = io(h, B * 6 * 4);
+      h += up(B * 6 * 4);
+      q->h_out = reinterpret_cast<float*>(h);
+      h += up(B * q->npix * 4);
+      q->h_fixed = reinterpret_cast<float*>(h);
+      h += up(B * q->npix * 4);
+      q->h_gpose = reinterpret_cast<float*>(h);
+      q->d_gpose = io(h, B * 6 * 4);
+      h += up(B * 6 * 4);
+      q->h_loss = reinterpret_cast<float*>(h);
+      q->d_loss = io(h, B * 4);
+      std::memcpy(q->h_poses, q->r.poses, B * 6 * 4);
+      std::memcpy(q->h_fixed, q->r.fixed, B * q->npix * 4);
+      rq[i] = drr::ServeRequest{};  // no table entry of the walk (its status word stays as uploaded)
+      continue;
+    }
     q->h_poses = reinterpret_cast<float*>(h);
     q->d_poses = io(h, P * 6 * 4);
     h += up(P * 6 * 4);
@@ -381,13 +441,13 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     sr.tile_start = tstart[i];
     sr.pose_start = pstart[i];
   }
-  hdr->nreq = static_cast<int>(batch.size());
+  hdr->nreq = nw;
   hdr->total_tiles = total_tiles;
   hdr->total_poses = total_poses;
   hdr->pad_ = 0;
   auto* h_status = reinterpret_cast<unsigned int*>(st.h_table + status_off);
   for (size_t i = 0; i < batch.size(); ++i) h_status[i] = batch[i]->inject_status;  // normally 0
-  const size_t tbytes = sizeof(drr::ServeHeader) + batch.size() * sizeof(drr::ServeRequest);
+  const size_t tbytes = sizeof(drr::ServeHeader) + size_t(nw) * sizeof(drr::ServeRequest);
   const size_t sbytes = batch.size() * sizeof(unsigned int);
   // The table set and the request buffers written here belong to no tick still
   // in flight: this tick's set was last used `depth` ticks ago, which has finished
@@ -397,9 +457,13 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(st.d_table + status_off, h_status, sbytes, cudaMemcpyHostToDevice, h2d);
   for (Req* q : batch) {
-    if (e != cudaSuccess || kHostIo) break;
-    e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->nposes) * 6 * 4, cudaMemcpyHostToDevice, h2d);
-    if (e == cudaSuccess && q->grad)
+    if (e != cudaSuccess) break;
+    if (q->zncc)  // the ZNCC kernel reads each fixed image whole: from device memory
+      e = cudaMemcpyAsync(q->d_fixed, q->h_fixed, size_t(q->r.B) * q->npix * 4, cudaMemcpyHostToDevice, h2d);
+    if (kHostIo) continue;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(q->d_poses, q->h_poses, size_t(q->nposes) * 6 * 4, cudaMemcpyHostToDevice, h2d);
+    if (e == cudaSuccess && q->grad && !q->zncc)
       e = cudaMemcpyAsync(q->d_grad, q->h_grad, size_t(q->r.B) * q->npix * 4, cudaMemcpyHostToDevice, h2d);
   }
   if (e == cudaSuccess) e = cudaEventRecord(st.in_ready, h2d);
@@ -409,8 +473,14 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     if (e == cudaSuccess) e = launch_plain(*batch[0], st.ks);
     if (e == cudaSuccess) drr::count_launches(batch[0]->grad ? 4 : 2);
   } else {
-    if (e == cudaSuccess) e = launch_kernels(t->set);
-    if (e == cudaSuccess) drr::count_launches(3);
+    if (nw > 0) {
+      if (e == cudaSuccess) e = launch_kernels(t->set);
+      if (e == cudaSuccess) drr::count_launches(3);
+    }
+    for (int i = nw; i < n && e == cudaSuccess; ++i) {
+      e = launch_registration_step(*batch[i], st.ks);
+      if (e == cudaSuccess) drr::count_launches(4);
+    }
   }
   if (e == cudaSuccess) e = cudaEventRecord(st.stop, st.ks);
   if (e == cudaSuccess) t->timed = true;
@@ -418,10 +488,16 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h_status, st.d_table + status_off, sbytes, cudaMemcpyDeviceToHost, d2h);
   for (Req* q : batch) {
-    if (e != cudaSuccess || kHostIo) break;
-    e = cudaMemcpyAsync(q->h_out, q->d_out, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, d2h);
+    if (e != cudaSuccess) break;
+    if (q->zncc)  // E stays on the device for the ZNCC kernel; it comes down here
+      e = cudaMemcpyAsync(q->h_out, q->d_e, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, d2h);
+    if (kHostIo) continue;
+    if (e == cudaSuccess && !q->zncc)
+      e = cudaMemcpyAsync(q->h_out, q->d_out, size_t(q->r.B) * q->npix * 4, cudaMemcpyDeviceToHost, d2h);
     if (e == cudaSuccess && q->grad)
       e = cudaMemcpyAsync(q->h_gpose, q->d_gpose, size_t(q->r.B) * 6 * 4, cudaMemcpyDeviceToHost, d2h);
+    if (e == cudaSuccess && q->zncc)
+      e = cudaMemcpyAsync(q->h_loss, q->d_loss, size_t(q->r.B) * 4, cudaMemcpyDeviceToHost, d2h);
   }
   if (e == cudaSuccess) e = cudaLaunchHostFunc(d2h, tick_done, t);
   if (e != cudaSuccess) {
@@ -457,6 +533,7 @@ void drr_server_s::copy_result(Tick* t, size_t i) {
   }
   std::memcpy(q->r.drr_out, q->h_out, size_t(q->r.B) * q->npix * 4);
   if (q->grad) std::memcpy(q->r.grad_pose_out, q->h_gpose, size_t(q->r.B) * 6 * 4);
+  if (q->zncc) std::memcpy(q->r.loss_out, q->h_loss, size_t(q->r.B) * 4);
 }
 
 // Called with the lock held after copy_result: the request is done (its
@@ -610,10 +687,21 @@ drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* tic
   if (!req->poses || !req->drr_out) return drr::set_error(DRR_ERR_INVALID, "poses and drr_out are required");
   if (req->grad_drr && !req->grad_pose_out)
     return drr::set_error(DRR_ERR_INVALID, "grad_pose_out is required with grad_drr");
+  if (req->fixed) {
+    if (req->grad_drr) return drr::set_error(DRR_ERR_INVALID, "a request takes grad_drr or fixed, not both");
+    if (!req->grad_pose_out || !req->loss_out)
+      return drr::set_error(DRR_ERR_INVALID, "grad_pose_out and loss_out are required with fixed");
+    if (s->cfg.plain_fp32_baseline)
+      return drr::set_error(DRR_ERR_INVALID, "the comparison server takes no registration-step requests");
+    if (!(req->zncc_eps >= 0.f) || !std::isfinite(req->zncc_eps))
+      return drr::set_error(DRR_ERR_INVALID, "zncc_eps must be finite and >= 0");
+  }
   Req* q = new Req();
   q->r = *req;
+  if (req->fixed && q->r.zncc_eps == 0.f) q->r.zncc_eps = 1e-8f;
   q->det = dd;
-  q->grad = req->grad_drr != nullptr;
+  q->grad = req->grad_drr != nullptr || req->fixed != nullptr;
+  q->zncc = req->fixed != nullptr;
   q->npix = size_t(dd.H) * dd.W;
   if (size_t(req->B) * size_t(drr::pose_tiles(dd)) >= (size_t(1) << 30)) {
     delete q;

@@ -61,7 +61,8 @@ class drr_server_config(ctypes.Structure):
 class drr_request(ctypes.Structure):
     _fields_ = [("volume", ctypes.c_void_p), ("detector", drr_detector), ("B", ctypes.c_int32),
                 ("poses", ctypes.c_void_p), ("grad_drr", ctypes.c_void_p), ("drr_out", ctypes.c_void_p),
-                ("grad_pose_out", ctypes.c_void_p)]
+                ("grad_pose_out", ctypes.c_void_p), ("fixed", ctypes.c_void_p), ("loss_out", ctypes.c_void_p),
+                ("zncc_eps", ctypes.c_float)]
 
 
 class drr_result(ctypes.Structure):
@@ -495,11 +496,12 @@ class Arena:
 class Ticket:
     """A submitted request: owns its host buffers until wait() returns."""
 
-    def __init__(self, server, tid, out, grad_pose, keep):
+    def __init__(self, server, tid, out, grad_pose, keep, loss=None):
         self.server = server
         self.id = tid
         self.out = out
         self.grad_pose = grad_pose
+        self.loss = loss
         self._keep = keep
         self.result = None
 
@@ -512,6 +514,8 @@ class Ticket:
         self._keep = None
         if st != 0:
             raise DrrError(st, self.server._lib.drr_last_error().decode())
+        if self.loss is not None:
+            return self.out, self.grad_pose, self.loss
         return self.out, self.grad_pose
 
     def cancel(self):
@@ -542,7 +546,10 @@ class Server:
         self.h = ctypes.c_void_p()
         check(self._lib.drr_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
 
-    def submit(self, volume: Volume, det, poses, grad=None) -> Ticket:
+    def submit(self, volume: Volume, det, poses, grad=None, fixed=None, eps: float = 1e-8) -> Ticket:
+        """Queue a render (grad=None, fixed=None), a render with the pose gradient of the
+        upstream gradient `grad`, or a registration step against the fixed images `fixed`
+        (loss -ZNCC and its pose gradient; wait() then returns (E, dL/d eta, loss))."""
         d = detector(det)
         poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 6)
         B = poses.shape[0]
@@ -556,9 +563,19 @@ class Server:
             keep += [grad, gpose]
             req.grad_drr = grad.ctypes.data
             req.grad_pose_out = gpose.ctypes.data
+        loss = None
+        if fixed is not None:
+            fixed = np.ascontiguousarray(fixed, dtype=np.float32).reshape(B, d.height, d.width)
+            gpose = np.empty((B, 6), np.float32)
+            loss = np.empty(B, np.float32)
+            keep += [fixed, gpose, loss]
+            req.fixed = fixed.ctypes.data
+            req.grad_pose_out = gpose.ctypes.data
+            req.loss_out = loss.ctypes.data
+            req.zncc_eps = float(eps)
         tid = ctypes.c_uint64()
         check(self._lib.drr_server_submit(self.h, ctypes.byref(req), ctypes.byref(tid)))
-        return Ticket(self, tid.value, out, gpose, keep)
+        return Ticket(self, tid.value, out, gpose, keep, loss)
 
     def pause(self, paused: bool = True):
         """Stop (or resume) admitting queued requests; running ticks finish."""

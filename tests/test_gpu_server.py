@@ -325,6 +325,63 @@ def test_two_threads_wait_on_one_ticket(drr, vols):
     srv.close()
 
 
+def _registration_direct(drr, vol, det, poses_np, fixed_np, eps=1e-8):
+    poses = torch.from_numpy(poses_np).cuda()
+    E, J = drr.render(vol, det, poses, jacobian=True)
+    loss, g = drr.zncc(E, torch.from_numpy(fixed_np).cuda(), eps=eps)
+    G = drr.render_backward(vol, det, poses, g, jac=J)
+    return E.cpu().numpy(), G.cpu().numpy(), loss.cpu().numpy()
+
+
+def test_registration_step_requests(drr, vols):
+    # registration steps (fixed images in, -ZNCC and its pose gradient out) served in the
+    # same ticks as renders and gradient requests: every result is the direct calls' bits,
+    # and the loss and gradient match the oracle's render -> ZNCC -> pose gradient
+    data, sp, vol = vols["hu"]
+    det = inputs.Detector(300.0, 37, 41, 1.6, 1.7)
+    truth = inputs.random_poses(3, seed=440)
+    fixed = drr.render(vol, det, torch.from_numpy(truth).cuda()).cpu().numpy()
+    moving = truth + inputs.pose_offsets(3, seed=441, max_angle_deg=5, max_trans_mm=5)
+    srv = drr.Server(device_budget=64 << 20)
+    srv.pause(True)  # everything below lands in one tick
+    t_reg = srv.submit(vol, det, moving, fixed=fixed)
+    t_reg1 = srv.submit(vol, det, moving[:1], fixed=fixed[:1], eps=1e-6)
+    g = inputs.upstream_grad((2, 37, 41), seed=442)
+    t_grad = srv.submit(vol, det, moving[:2], g)
+    t_ren = srv.submit(vol, det, moving)
+    srv.pause(False)
+    E, G, L = t_reg.wait(20000)
+    E1, G1, L1 = t_reg1.wait(20000)
+    Eg, Gg = t_grad.wait(20000)
+    Er, _ = t_ren.wait(20000)
+    assert t_reg.result.tick == t_grad.result.tick == t_ren.result.tick
+    E_d, G_d, L_d = _registration_direct(drr, vol, det, moving.astype(np.float32), fixed)
+    np.testing.assert_array_equal(E, E_d)
+    np.testing.assert_array_equal(G, G_d)
+    np.testing.assert_array_equal(L, L_d)
+    E_d1, G_d1, L_d1 = _registration_direct(drr, vol, det, moving[:1].astype(np.float32), fixed[:1], eps=1e-6)
+    np.testing.assert_array_equal(G1, G_d1)
+    np.testing.assert_array_equal(L1, L_d1)
+    Eg_d, Gg_d = _direct(drr, vol, det, moving[:2].astype(np.float32), g)
+    np.testing.assert_array_equal(Gg, Gg_d)
+    np.testing.assert_array_equal(Er, _direct(drr, vol, det, moving.astype(np.float32))[0])
+    # against the oracle (which renders its own fixed images) on the BF16-stored volume
+    ov = ovol(oracle.round_bf16(oracle.hu_to_mu(data, inputs.MU_WATER).astype(np.float32)), sp)
+    F_ref = oracle.render(ov, odet(det), truth)
+    E_ref = oracle.render(ov, odet(det), moving.astype(np.float32))
+    np.testing.assert_allclose(L, oracle.zncc_loss(E_ref, F_ref, 1e-8), atol=1e-5)
+    G_ref = oracle.pose_grad(ov, odet(det), moving.astype(np.float32), oracle.zncc_loss_grad(E_ref, F_ref, 1e-8))
+    assert grad_err(G, G_ref).max() < GRAD_TOL
+    # argument errors: both kinds of gradient at once; the comparison server
+    with pytest.raises(drr.DrrError):
+        srv.submit(vol, det, moving[:2], g, fixed=fixed[:2])
+    srv.close()
+    plain = drr.Server(device_budget=64 << 20, plain_fp32_baseline=True)
+    with pytest.raises(drr.DrrError):
+        plain.submit(vol, det, moving, fixed=fixed)
+    plain.close()
+
+
 def test_tick_work_cap_bounds_each_tick(drr, vols):
     # a cap of about two requests' work per tick: a backlog of equal requests goes
     # into ticks of at most two, a request larger than the cap alone, and every
