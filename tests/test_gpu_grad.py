@@ -338,3 +338,39 @@ def test_autograd_through_volume_and_poses(drr):
     P3 = torch.from_numpy(poses_np).cuda().requires_grad_(True)
     (drr.drr_volume(torch.from_numpy(mu_np).cuda(), sp, det, P3) * w).sum().backward()
     assert torch.equal(P3.grad, P.grad)
+
+
+def test_non_finite_poses(drr):
+    # a pose with a NaN or infinite parameter gives NaN for every pixel of its DRR, its
+    # Jacobian and its pose gradient, zero segments, and no back-projection adds; the other
+    # poses of the batch keep their bits
+    mu, sp, det, poses_np = _case_small_ct()
+    vol = drr.Volume(mu, sp)
+    bad = poses_np.copy()
+    bad[1, 0] = np.nan
+    bad[2, 4] = np.inf
+    poses = torch.from_numpy(bad).cuda()
+    g_np = inputs.upstream_grad((3, det.height, det.width), seed=60)
+    g = torch.from_numpy(g_np).cuda()
+    E, J = drr.render(vol, det, poses, jacobian=True)
+    F = drr.render(vol, det, poses)
+    G = drr.render_backward(vol, det, poses, g, jac=J).cpu().numpy()
+    G_walk = drr.render_backward(vol, det, poses, g).cpu().numpy()
+    gv = torch.zeros(mu.shape, device="cuda")
+    drr.render_backward(vol, det, poses, g, pose_grad=False, grad_volume=gv)
+    n = drr.count_segments(vol, det, poses).cpu().numpy()
+    E, J, F = E.cpu().numpy(), J.cpu().numpy(), F.cpu().numpy()
+    for b in (1, 2):
+        assert np.isnan(E[b]).all() and np.isnan(J[b]).all() and np.isnan(F[b]).all()
+        assert np.isnan(G[b]).all() and np.isnan(G_walk[b]).all()
+        assert (n[b] == 0).all()
+    one = torch.from_numpy(poses_np[:1]).cuda()
+    E1, J1 = drr.render(vol, det, one, jacobian=True)
+    np.testing.assert_array_equal(F[0], drr.render(vol, det, one).cpu().numpy()[0])
+    np.testing.assert_array_equal(G_walk[0], drr.render_backward(vol, det, one, g[:1]).cpu().numpy()[0])
+    np.testing.assert_array_equal(n[0], drr.count_segments(vol, det, one).cpu().numpy()[0])
+    gv1 = torch.zeros(mu.shape, device="cuda")
+    drr.render_backward(vol, det, one, g[:1], pose_grad=False, grad_volume=gv1)
+    gv, gv1 = gv.cpu().numpy(), gv1.cpu().numpy()
+    assert np.isfinite(gv).all()
+    np.testing.assert_allclose(gv, gv1, rtol=1e-5, atol=1e-6 * np.abs(gv1).max())
