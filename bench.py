@@ -433,17 +433,55 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
                      "at_half_own_saturation": own, "at_product_headline_rate": same,
                      "what": "drr_server with plain_fp32_baseline: one request per tick, plain FP32 forward walk, "
                              "gradients by central differences (13 renders per pose); same request mix"}
+    reg = registration_step_latency(drr, vols)
     return {"p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "mean_ms": head["mean_ms"],
             "requests": head["requests"], "offered_rate_per_s": head["offered_rate_per_s"],
             "achieved_drrs_per_s": head["achieved_drrs_per_s"], "saturation_drrs_per_s": sat_rate,
             "saturation_p50_ms": float(np.percentile(lat_sat, 50)), "saturation_passes_per_s": rates,
             "ticks": head["ticks"],
             "gpu_busy_frac": head["gpu_busy_frac"], "by_load": runs, "plain_fp32_server": plain_res,
+            "registration_step": reg,
             "max_tick_work": max_tick_work,
             "tick_depth": tick_depth or 3,
             "workload": "8 resident volumes {128^3, 256^3, 512x512x133, 512x512x300} x {FP32, BF16}; one pose per "
                         "request; detector H=W~U{128..512} at 280/H mm, SDR 510; 50% render+pose-grad; Poisson "
                         "arrivals at the listed fractions of the measured saturation rate (headline: 50%)"}
+
+
+def registration_step_latency(drr, vols, n=256, reps=20):
+    """A lone registration-step request (fixed image in; E, -ZNCC and its pose gradient out)
+    on the 512x512x133 FP32 volume at n x n, served one at a time: median submit->result
+    latency, beside the same step as direct calls from host data (median wall time, synchronised)."""
+    import torch
+    from paper_2208_12737_gb300 import inputs
+    vol = dict(vols)["512x512x133/f32"]
+    det = inputs.Detector(510.0, n, n, 280.0 / n, 280.0 / n)
+    truth = inputs.random_poses(1, seed=77)
+    fixed = drr.render(vol, det, torch.from_numpy(truth).cuda()).cpu().numpy()
+    moving = (truth + inputs.pose_offsets(1, seed=78, max_angle_deg=5, max_trans_mm=5)).astype(np.float32)
+    srv = drr.Server(device_budget=1 << 30)
+    lat = []
+    for i in range(reps + 3):
+        t = srv.submit(vol, det, moving, fixed=fixed)
+        t.wait(60000)
+        if i >= 3:
+            lat.append(t.result.latency_ms)
+    srv.close()
+    fixed_d = torch.from_numpy(fixed).cuda()
+    direct = []
+    for i in range(reps + 3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        poses = torch.from_numpy(moving).cuda()
+        E, J = drr.render(vol, det, poses, jacobian=True)
+        loss, g = drr.zncc(E, fixed_d)
+        G = drr.render_backward(vol, det, poses, g, jac=J)
+        E.cpu(), G.cpu(), loss.cpu()
+        if i >= 3:
+            direct.append((time.perf_counter() - t0) * 1e3)
+    return {"served_p50_ms": statistics.median(lat), "direct_calls_ms": statistics.median(direct),
+            "workload": f"512x512x133 CT (FP32), {n}x{n} @ {280.0 / n:.3g} mm, one pose, -ZNCC against a "
+                        "rendered fixed image (fixed image resident on the device for the direct calls)"}
 
 
 def l2_read_gbs(drr, mb=64, reps=20):
