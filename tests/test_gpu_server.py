@@ -281,7 +281,7 @@ def test_destroy_while_threads_wait(drr, vols):
     for th in threads:
         th.start()
     import time
-    time.sleep(0.2)
+    time.sleep(0.5)  # the waiter threads are inside drr_server_wait by then
     srv.close()
     for th in threads:
         th.join(timeout=30)
@@ -311,7 +311,7 @@ def test_two_threads_wait_on_one_ticket(drr, vols):
     threads = [threading.Thread(target=waiter) for _ in range(2)]
     for th in threads:
         th.start()
-    time.sleep(0.2)
+    time.sleep(0.5)  # the waiter threads are inside drr_server_wait by then
     srv.pause(False)
     for th in threads:
         th.join(timeout=30)
