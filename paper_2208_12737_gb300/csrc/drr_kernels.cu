@@ -1872,16 +1872,18 @@ int grid_for(int64_t n, int threads) {
 template <int MODE, int DT>
 int resident_blocks() {
   constexpr int kMaxDev = 64;
-  static int cache[kMaxDev] = {0};
+  static std::atomic<int> cache[kMaxDev] = {};  // calls from several host threads may race to fill it
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = 0;
-  if (cache[dev] == 0) {
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, siddon_kernel<MODE, DT>, kThreads, 0);
-    cache[dev] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    v = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    cache[dev].store(v, std::memory_order_relaxed);
   }
-  return cache[dev];
+  return v;
 }
 
 // The split kernel with K warps per tile: its dynamic shared memory (the chunk
@@ -1891,10 +1893,11 @@ constexpr size_t kSplitSmem = static_cast<size_t>(kSplitMaxChunks) * 32 * sizeof
 template <int DT, int K>
 int split_resident_blocks() {
   constexpr int kMaxDev = 64;
-  static int cache[kMaxDev] = {0};
+  static std::atomic<int> cache[kMaxDev] = {};  // calls from several host threads may race to fill it
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
-  if (cache[dev] == 0) {
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaFuncSetAttribute(siddon_split_kernel<DT, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1902,12 +1905,13 @@ int split_resident_blocks() {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, siddon_split_kernel<DT, K>, 32 * K, kSplitSmem) !=
             cudaSuccess) {
       cudaGetLastError();
-      cache[dev] = -1;
+      v = -1;
     } else {
-      cache[dev] = per_sm > 0 ? sms * per_sm : -1;
+      v = per_sm > 0 ? sms * per_sm : -1;
     }
+    cache[dev].store(v, std::memory_order_relaxed);
   }
-  return cache[dev] > 0 ? cache[dev] : 0;
+  return v > 0 ? v : 0;
 }
 
 template <int DT, int K>
