@@ -616,7 +616,7 @@ def _autograd():
         def backward(ctx, grad):
             poses, J = ctx.saved_tensors
             g = render_backward(ctx.volume, ctx.det, poses.contiguous(), grad.contiguous().float(), jac=J)
-            return g, None, None
+            return g.to(poses.device), None, None  # pinned host poses get a host gradient
 
     class DRRVolumeFunction(torch.autograd.Function):
         """(mu (nz, ny, nx), poses (B, 6)) -> DRR (B, H, W).  E is linear in the volume
@@ -642,7 +642,7 @@ def _autograd():
             g = grad.contiguous().float()
             g_mu = g_pose = None
             if ctx.needs_input_grad[1]:
-                g_pose = render_backward(ctx.volume, ctx.det, poses, g, jac=J)
+                g_pose = render_backward(ctx.volume, ctx.det, poses, g, jac=J).to(poses.device)
             if ctx.needs_input_grad[0]:
                 g_mu = torch.zeros(ctx.volume.shape_zyx, device=g.device, dtype=torch.float32)
                 render_backward(ctx.volume, ctx.det, poses, g, pose_grad=False, grad_volume=g_mu)

@@ -92,3 +92,16 @@ def test_pageable_and_misplaced_buffers_are_rejected(drr, case):
     with pytest.raises(TypeError):
         drr.render(vol, det, torch.from_numpy(poses_np))
     drr.stream_check()
+
+
+def test_autograd_with_pinned_host_poses(drr, case):
+    # drr.drr on pinned host poses: E on the device, dL/d poses back on the host, equal to
+    # the device-pose gradient
+    vol, det, poses_np, g_np = case
+    p_dev = torch.from_numpy(poses_np).cuda().requires_grad_(True)
+    p_host = torch.from_numpy(poses_np).pin_memory().requires_grad_(True)
+    g = torch.from_numpy(g_np).cuda()
+    (drr.drr(vol, det, p_dev) * g).sum().backward()
+    (drr.drr(vol, det, p_host) * g).sum().backward()
+    assert p_host.grad.device.type == "cpu"
+    np.testing.assert_array_equal(p_host.grad.numpy(), p_dev.grad.cpu().numpy())
