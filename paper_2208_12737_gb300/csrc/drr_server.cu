@@ -126,6 +126,14 @@ bool layout_tick(int n, const int32_t* B, const drr::DetDev* det, int32_t* tile_
 #define DRR_SERVE_HOST_IO 1
 #endif
 constexpr bool kHostIo = DRR_SERVE_HOST_IO != 0;
+// How the loop learns that a tick is done: the tick's completion event (queried
+// by the loop), and a host function enqueued after the tick that wakes the loop.
+// With spin_poll_us > 0 in the configuration, while a single tick is in flight
+// the loop polls that event instead of sleeping, yielding the core between
+// queries, for up to that long (a submission ends the spin early): a lone
+// request's results come back without the host function's wake-up latency.
+// With two or more ticks in flight it sleeps until woken, so requests that
+// arrive meanwhile gather into the next tick.
 
 void size_request(Req& q, bool plain) {
   const size_t B = static_cast<size_t>(q.r.B);
@@ -171,6 +179,8 @@ struct drr_server_s {
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t start = nullptr, stop = nullptr;  // around the kernels; stop also orders the result copies
     cudaEvent_t in_ready = nullptr;               // the tick's inputs are on the device
+    cudaEvent_t done_ev = nullptr;                // after the tick's last kernel and copy
+    unsigned int* status_dev = nullptr;           // the status words as the kernels address them
     cudaStream_t ks = nullptr;                    // the kernel stream (shared by all sets)
   } sets[kMaxTickSets];
   int depth = 3;  // ticks in flight at most (table sets in use)
@@ -178,6 +188,7 @@ struct drr_server_s {
   size_t status_off = 0;  // offset of the status words in a table
   int walk_grid = 1;
   int waiters = 0;  // threads inside drr_server_wait (destroy waits for them to leave)
+  std::atomic<uint64_t> submit_seq{0};  // bumped by every submission (ends the loop's poll early)
 
   std::mutex mu;
   std::condition_variable cv_loop, cv_done;
@@ -220,19 +231,16 @@ struct drr_server_s {
   cudaError_t launch_kernels(int set);
   cudaError_t launch_plain(const Req& q, cudaStream_t ks);
   cudaError_t launch_registration_step(const Req& q, cudaStream_t ks);
+  bool tick_ready(Tick* t);
 };
 
 namespace {
 
-// Runs on a CUDA runtime thread once the tick's stream work is complete.  It
-// takes no lock (so it never stalls the stream behind the loop thread); the
-// loop re-checks the flag at least every 200 us.
-void CUDART_CB tick_done(void* p) {
-  Tick* t = static_cast<Tick*>(p);
-  drr_server_s* s = t->owner;
-  t->done.store(true);
-  s->cv_loop.notify_all();
-}
+// Runs on a CUDA runtime thread once a tick's stream work is complete: it wakes
+// the loop, which decides completion from the tick's event (the tick itself may
+// already be gone).  It takes no lock, so it never stalls the stream behind the
+// loop thread; the loop re-checks at least every 200 us anyway.
+void CUDART_CB tick_done(void* p) { static_cast<drr_server_s*>(p)->cv_loop.notify_all(); }
 
 }  // namespace
 
@@ -241,8 +249,7 @@ cudaError_t drr_server_s::launch_kernels(int set) {
   if (st.graph) return cudaGraphLaunch(st.graph, st.ks);
   const auto* hdr = reinterpret_cast<const drr::ServeHeader*>(st.d_table);
   const auto* rq = reinterpret_cast<const drr::ServeRequest*>(st.d_table + sizeof(drr::ServeHeader));
-  auto* status = reinterpret_cast<unsigned int*>(st.d_table + status_off);
-  return drr::launch_serve_tick(hdr, rq, status, st.d_counter, cfg.max_tick_poses, walk_grid, st.ks);
+  return drr::launch_serve_tick(hdr, rq, st.status_dev, st.d_counter, cfg.max_tick_poses, walk_grid, st.ks);
 }
 
 // The comparison server's tick: one request, the plain FP32 forward walk over
@@ -454,7 +461,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   // (its result copies, after its kernels, are done), and the arenas hand out
   // only memory of finished ticks.
   if (e == cudaSuccess) e = cudaMemcpyAsync(st.d_table, st.h_table, tbytes, cudaMemcpyHostToDevice, h2d);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !kHostIo)  // with host I/O the kernels use the words in place
     e = cudaMemcpyAsync(st.d_table + status_off, h_status, sbytes, cudaMemcpyHostToDevice, h2d);
   for (Req* q : batch) {
     if (e != cudaSuccess) break;
@@ -485,7 +492,7 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
   if (e == cudaSuccess) e = cudaEventRecord(st.stop, st.ks);
   if (e == cudaSuccess) t->timed = true;
   if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, st.stop, 0);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !kHostIo)
     e = cudaMemcpyAsync(h_status, st.d_table + status_off, sbytes, cudaMemcpyDeviceToHost, d2h);
   for (Req* q : batch) {
     if (e != cudaSuccess) break;
@@ -499,7 +506,8 @@ bool drr_server_s::form_tick(std::unique_lock<std::mutex>& lk) {
     if (e == cudaSuccess && q->zncc)
       e = cudaMemcpyAsync(q->h_loss, q->d_loss, size_t(q->r.B) * 4, cudaMemcpyDeviceToHost, d2h);
   }
-  if (e == cudaSuccess) e = cudaLaunchHostFunc(d2h, tick_done, t);
+  if (e == cudaSuccess) e = cudaEventRecord(st.done_ev, d2h);
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(d2h, tick_done, this);
   if (e != cudaSuccess) {
     // the tick could not be enqueued completely: let what was queued drain, then fail its requests
     sync_streams();
@@ -555,11 +563,21 @@ void drr_server_s::finish_request(Req* q) {
   cv_done.notify_all();
 }
 
+// Whether a tick's work is complete (or failed: its requests then fail when
+// their results are read).  Called by the loop thread only.
+bool drr_server_s::tick_ready(Tick* t) {
+  if (!t->done.load()) {
+    const cudaError_t q = cudaEventQuery(sets[t->set].done_ev);
+    if (q != cudaErrorNotReady) t->done.store(true);
+  }
+  return t->done.load();
+}
+
 void drr_server_s::run() {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lk(mu);
   for (;;) {
-    while (!inflight.empty() && inflight.front()->done.load()) {
+    while (!inflight.empty() && tick_ready(inflight.front())) {
       Tick* t = inflight.front();
       inflight.pop_front();
       if (t->timed) {
@@ -579,9 +597,29 @@ void drr_server_s::run() {
     if (stop && inflight.empty()) break;
     bool launched = false;
     if (!stop && !paused && static_cast<int>(inflight.size()) < depth && !pending.empty()) launched = form_tick(lk);
+    if (!launched && cfg.spin_poll_us > 0 && inflight.size() == 1) {
+      // one tick in flight: poll its completion event without the lock
+      Tick* f = inflight.front();
+      const cudaEvent_t ev = sets[f->set].done_ev;
+      const uint64_t seq = submit_seq.load();
+      lk.unlock();
+      const auto t0 = Clock::now();
+      bool ready = false;
+      for (;;) {
+        if (cudaEventQuery(ev) != cudaErrorNotReady) {
+          ready = true;
+          break;
+        }
+        if (submit_seq.load() != seq) break;
+        if (Clock::now() - t0 > std::chrono::microseconds(cfg.spin_poll_us)) break;
+        std::this_thread::yield();
+      }
+      lk.lock();
+      if (ready || submit_seq.load() != seq) continue;
+    }
     if (!launched) {
       cv_loop.wait_for(lk, std::chrono::microseconds(200), [this] {
-        return stop || (!inflight.empty() && inflight.front()->done.load()) ||
+        return stop || (!inflight.empty() && tick_ready(inflight.front())) ||
                (!paused && static_cast<int>(inflight.size()) < depth && !pending.empty());
       });
     }
@@ -605,6 +643,8 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
   if (cfg.tick_depth == 0) cfg.tick_depth = 3;
   if (cfg.tick_depth < 2 || cfg.tick_depth > kMaxTickSets)
     return drr::set_error(DRR_ERR_INVALID, "tick_depth must be in [2, %d]", kMaxTickSets);
+  if (cfg.spin_poll_us < 0 || cfg.spin_poll_us > 1000000)
+    return drr::set_error(DRR_ERR_INVALID, "spin_poll_us must be in [0, 10^6]");
   drr_server_s* s = new drr_server_s();
   s->cfg = cfg;
   cudaError_t e = cudaSuccess;
@@ -620,13 +660,23 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
   s->table_bytes = s->status_off + size_t(cfg.max_inflight) * sizeof(unsigned int);
   s->depth = cfg.tick_depth;
   for (int i = 0; i < s->depth && e == cudaSuccess; ++i) {
-    e = cudaHostAlloc(reinterpret_cast<void**>(&s->sets[i].h_table), s->table_bytes, 0);
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s->sets[i].h_table), s->table_bytes, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->sets[i].d_table), s->table_bytes);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->sets[i].d_counter), sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->sets[i].d_table, 0, s->table_bytes);
     if (e == cudaSuccess) e = cudaEventCreate(&s->sets[i].start);
     if (e == cudaSuccess) e = cudaEventCreate(&s->sets[i].stop);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->sets[i].in_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->sets[i].done_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+      if (kHostIo) {
+        char* mapped = nullptr;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&mapped), s->sets[i].h_table, 0);
+        if (e == cudaSuccess) s->sets[i].status_dev = reinterpret_cast<unsigned int*>(mapped + s->status_off);
+      } else {
+        s->sets[i].status_dev = reinterpret_cast<unsigned int*>(s->sets[i].d_table + s->status_off);
+      }
+    }
     // one kernel stream for every set: ticks run one after another.  (A stream
     // per set, so that consecutive ticks overlap, measured slower: saturation
     // 8.6k-9.2k against 12.1k-13.7k requests/s on the serving mix, the
@@ -658,6 +708,7 @@ drr_status drr_server_create(const drr_server_config* cfg_in, drr_server* out) {
       if (st2.start) cudaEventDestroy(st2.start);
       if (st2.stop) cudaEventDestroy(st2.stop);
       if (st2.in_ready) cudaEventDestroy(st2.in_ready);
+      if (st2.done_ev) cudaEventDestroy(st2.done_ev);
     }
     if (s->sets[0].ks) cudaStreamDestroy(s->sets[0].ks);
     if (s->dev_base) cudaFree(s->dev_base);
@@ -738,6 +789,7 @@ drr_status drr_server_submit(drr_server s, const drr_request* req, uint64_t* tic
     s->reqs[q->id] = q;
     s->pending.push_back(q);
     ++s->submitted;
+    s->submit_seq.fetch_add(1);
     *ticket = q->id;
   }
   s->cv_loop.notify_all();
@@ -896,6 +948,7 @@ drr_status drr_server_destroy(drr_server s) {
     if (st.start) cudaEventDestroy(st.start);
     if (st.stop) cudaEventDestroy(st.stop);
     if (st.in_ready) cudaEventDestroy(st.in_ready);
+    if (st.done_ev) cudaEventDestroy(st.done_ev);
   }
   if (s->sets[0].ks) cudaStreamDestroy(s->sets[0].ks);
   cudaFree(s->dev_base);

@@ -55,7 +55,7 @@ class drr_server_config(ctypes.Structure):
                 ("max_inflight", ctypes.c_int32), ("max_tick_poses", ctypes.c_int32),
                 ("use_cuda_graph", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("max_tick_work", ctypes.c_int64), ("plain_fp32_baseline", ctypes.c_int32),
-                ("tick_depth", ctypes.c_int32)]
+                ("tick_depth", ctypes.c_int32), ("spin_poll_us", ctypes.c_int32)]
 
 
 class drr_request(ctypes.Structure):
@@ -538,11 +538,12 @@ class Server:
 
     def __init__(self, device_budget: int = 512 << 20, host_budget: int = 0, max_inflight: int = 64,
                  max_tick_poses: int = 4096, use_cuda_graph: bool = True, device: int = -1,
-                 max_tick_work: int = 0, plain_fp32_baseline: bool = False, tick_depth: int = 0):
+                 max_tick_work: int = 0, plain_fp32_baseline: bool = False, tick_depth: int = 0,
+                 spin_poll_us: int = 0):
         self._lib = load()
         cfg = drr_server_config(device_budget, host_budget, max_inflight, max_tick_poses,
                                 1 if use_cuda_graph else 0, device, int(max_tick_work),
-                                1 if plain_fp32_baseline else 0, int(tick_depth))
+                                1 if plain_fp32_baseline else 0, int(tick_depth), int(spin_poll_us))
         self.h = ctypes.c_void_p()
         check(self._lib.drr_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
 

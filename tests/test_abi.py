@@ -115,7 +115,7 @@ def test_server_configs_are_checked_before_any_device_work(lib):
     lib = drr.load()
     out = ctypes.c_void_p()
     for field, value in (("tick_depth", 5), ("tick_depth", 1), ("max_tick_work", -1), ("max_inflight", 5000),
-                         ("max_tick_poses", (1 << 20) + 1)):
+                         ("max_tick_poses", (1 << 20) + 1), ("spin_poll_us", -1), ("spin_poll_us", 2_000_000)):
         cfg = drr.drr_server_config()
         setattr(cfg, field, value)
         assert lib.drr_server_create(ctypes.byref(cfg), ctypes.byref(out)) == 1, field

@@ -382,6 +382,22 @@ def test_registration_step_requests(drr, vols):
     plain.close()
 
 
+def test_spin_polling_server_gives_the_same_bits(drr, vols):
+    # a server that polls a lone tick's completion (spin_poll_us) returns the same results
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 40, 44, 1.5, 1.5)
+    g = inputs.upstream_grad((2, 40, 44), seed=451)
+    P = inputs.random_poses(2, seed=450)
+    out = []
+    for spin in (0, 500):
+        srv = drr.Server(device_budget=64 << 20, spin_poll_us=spin)
+        out.append([srv.submit(vol, det, P, g).wait(20000) for _ in range(3)])
+        srv.close()
+    for (E0, G0), (E1, G1) in zip(out[0], out[1]):
+        np.testing.assert_array_equal(E0, E1)
+        np.testing.assert_array_equal(G0, G1)
+
+
 def test_tick_work_cap_bounds_each_tick(drr, vols):
     # a cap of about two requests' work per tick: a backlog of equal requests goes
     # into ticks of at most two, a request larger than the cap alone, and every
