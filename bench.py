@@ -318,6 +318,18 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
     rng = np.random.default_rng(seed)
     grads = {}
 
+    # The client's result buffers: a few per detector size, allocated and touched
+    # once and reused round robin, as a client that keeps its buffers would (fresh
+    # arrays per request make the server's result copy take their page faults)
+    out_pool, out_next = {}, {}
+
+    def out_for(n):
+        if n not in out_pool:
+            out_pool[n] = [np.zeros((1, n, n), np.float32) for _ in range(4)]
+            out_next[n] = 0
+        out_next[n] = (out_next[n] + 1) % 4
+        return out_pool[n][out_next[n]]
+
     def make_req():
         name, v = vols[int(rng.integers(len(vols)))]
         n = int(rng.integers(128, 513))
@@ -328,7 +340,11 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
             if n not in grads:
                 grads[n] = inputs.upstream_grad((1, n, n), seed=n)
             g = grads[n]
-        return v, det, pose, g
+        return v, det, pose, g, out_for(n)
+
+    def submit(srv, r):
+        v, det, pose, g, out = r
+        return srv.submit(v, det, pose, g, out=out)
 
     def drain(tickets, lat):
         for t in tickets:
@@ -345,12 +361,12 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
         """Everything queued at once; after one untimed pass, the median of three timed passes."""
         srv = new_server(plain_mode)
         for r in reqs[:32]:
-            srv.submit(*r).wait(120000)
-        drain([srv.submit(*r) for r in reqs], [])
+            submit(srv, r).wait(120000)
+        drain([submit(srv, r) for r in reqs], [])
         rates, lat = [], []
         for _ in range(3):
             t0 = time.perf_counter()
-            tickets = [srv.submit(*r) for r in reqs]
+            tickets = [submit(srv, r) for r in reqs]
             lat_pass = []
             drain(tickets, lat_pass)
             rates.append(len(reqs) / (time.perf_counter() - t0))
@@ -379,7 +395,7 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
                 traces[frac] = (reqs, arrivals)
         srv = new_server(plain_mode)
         for r in reqs[:16]:
-            srv.submit(*r).wait(120000)
+            submit(srv, r).wait(120000)
         lat = []
         queue = []
         lock = threading.Condition()
@@ -402,7 +418,7 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
         for r, at in zip(reqs, arrivals):
             while time.perf_counter() - t0 < at:
                 pass
-            tk = srv.submit(*r)
+            tk = submit(srv, r)
             with lock:
                 queue.append(tk)
                 lock.notify()

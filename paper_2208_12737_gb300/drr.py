@@ -547,14 +547,20 @@ class Server:
         self.h = ctypes.c_void_p()
         check(self._lib.drr_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
 
-    def submit(self, volume: Volume, det, poses, grad=None, fixed=None, eps: float = 1e-8) -> Ticket:
+    def submit(self, volume: Volume, det, poses, grad=None, fixed=None, eps: float = 1e-8, out=None) -> Ticket:
         """Queue a render (grad=None, fixed=None), a render with the pose gradient of the
         upstream gradient `grad`, or a registration step against the fixed images `fixed`
-        (loss -ZNCC and its pose gradient; wait() then returns (E, dL/d eta, loss))."""
+        (loss -ZNCC and its pose gradient; wait() then returns (E, dL/d eta, loss)).
+        `out`: a C-contiguous float32 (B, H, W) array to receive E (reused buffers spare the
+        server's copy the page faults of fresh memory), else a new one."""
         d = detector(det)
         poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 6)
         B = poses.shape[0]
-        out = np.empty((B, d.height, d.width), np.float32)
+        if out is None:
+            out = np.empty((B, d.height, d.width), np.float32)
+        elif (not isinstance(out, np.ndarray) or out.dtype != np.float32 or out.shape != (B, d.height, d.width)
+              or not out.flags.c_contiguous or not out.flags.writeable):
+            raise ValueError(f"out must be a writeable C-contiguous float32 array of shape {(B, d.height, d.width)}")
         keep = [poses, out]
         req = drr_request(volume.handle, d, B, poses.ctypes.data, None, out.ctypes.data, None)
         gpose = None
