@@ -398,6 +398,25 @@ def test_spin_polling_server_gives_the_same_bits(drr, vols):
         np.testing.assert_array_equal(G0, G1)
 
 
+def test_caller_result_buffers(drr, vols):
+    # a request may name the array that receives its DRR; it gets the same bits as a
+    # fresh one, and a mis-shaped or mistyped array is refused before submission
+    data, sp, vol = vols["c"]
+    det = inputs.Detector(300.0, 21, 26, 1.5, 1.5)
+    P = inputs.random_poses(2, seed=460)
+    srv = drr.Server(device_budget=64 << 20)
+    mine = np.full((2, 21, 26), -7.0, np.float32)
+    E1, _ = srv.submit(vol, det, P, out=mine).wait(20000)
+    E2, _ = srv.submit(vol, det, P).wait(20000)
+    assert E1 is mine
+    np.testing.assert_array_equal(mine, E2)
+    for bad in (np.zeros((2, 21, 25), np.float32), np.zeros((2, 21, 26), np.float64),
+                np.zeros((2, 26, 21), np.float32).transpose(0, 2, 1)):
+        with pytest.raises(ValueError):
+            srv.submit(vol, det, P, out=bad)
+    srv.close()
+
+
 def test_tick_work_cap_bounds_each_tick(drr, vols):
     # a cap of about two requests' work per tick: a backlog of equal requests goes
     # into ticks of at most two, a request larger than the cap alone, and every
