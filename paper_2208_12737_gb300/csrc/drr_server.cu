@@ -2,18 +2,22 @@
 //
 // A host thread forms ticks.  Each tick admits queued requests in FIFO order
 // while request slots and the two explicit budgets (device buffers, pinned
-// staging) allow, stages their inputs, and runs one pose-setup, one persistent
-// ray-walk and one gradient-finalise launch covering all of their rays; the
-// three launches can be replayed from a CUDA graph captured at start-up (the
-// kernels read the tick's size from a device-resident table).  Up to
-// tick_depth ticks (3 by default) are in flight, so requests that arrive while
-// a tick is running are admitted into the next one, and an optional cap on the
-// work per tick bounds how long a tick runs.  Inputs go up on one copy stream and results come down on
-// another, ordered against the kernels' stream by events, so a tick's copies
-// overlap the neighbouring ticks' kernels.  A host function enqueued after each
-// tick's result copies marks it finished; the loop then writes results into
-// the callers' buffers (without the server lock, so submissions go on),
-// frees the tick's memory and wakes the waiters.
+// host buffers) allow, stages their inputs in the pinned host arena, and runs
+// one pose-setup, one persistent ray-walk and one gradient-finalise launch
+// covering all the rays of its renders and gradient requests; the three
+// launches can be replayed from a CUDA graph captured at start-up (the kernels
+// read the tick's size from a device-resident table).  Its registration-step
+// requests (fixed images in, -ZNCC and its pose gradient out) follow with the
+// direct calls' launches.  The kernels read the poses and upstream gradients
+// from, and write the DRRs, pose gradients and status words to, the mapped
+// pinned arena in place, so a tick has no input or result copies besides its
+// table.  Up to tick_depth ticks (3 by default) are in flight, so requests that
+// arrive while a tick is running are admitted into the next one, and an
+// optional cap on the work per tick bounds how long a tick runs.  The loop
+// learns that a tick is done from its event (woken by a host function after
+// the tick, or polling it when spin_poll_us is set and the tick is alone); it
+// then writes each request's results into its caller's buffers (without the
+// server lock, so submissions go on), frees its memory and wakes its waiter.
 //
 // Nothing on the device waits on the host: there are no spin loops in the
 // kernels, so a stalled client cannot hang the GPU.
