@@ -275,8 +275,9 @@ drr_status drr_probe_l2_read(const void* buf_dev, size_t bytes, int32_t reps, fl
 /* ---- serving: continuous batching of render / render+gradient requests ---- */
 /* No counterpart in the paper (whose method is a library call); this is the
  * request loop of the serving workload.  A host thread forms "ticks": it admits
- * queued requests while slots and the explicit memory budgets allow, uploads
- * their poses (and upstream gradients), and runs one pose-setup, one persistent
+ * queued requests while slots and the explicit memory budgets allow, stages
+ * their poses (and upstream gradients) in the server's pinned host memory, which
+ * the kernels read in place, and runs one pose-setup, one persistent
  * ray-walk and one gradient-finalise launch that cover the rays of every
  * admitted request, mixed volumes, dtypes and detectors included (optionally
  * replayed from a captured CUDA graph).  Several ticks can be in flight
@@ -286,7 +287,8 @@ drr_status drr_probe_l2_read(const void* buf_dev, size_t bytes, int32_t reps, fl
 
 typedef struct {
   size_t device_budget_bytes; /* device memory reserved for request buffers; 0 -> 512 MiB */
-  size_t host_budget_bytes;   /* pinned host staging; 0 -> the device budget */
+  size_t host_budget_bytes;   /* pinned host memory (mapped for the device) holding each request's
+                                 poses, upstream gradient and results; 0 -> the device budget */
   int32_t max_inflight;       /* requests admitted at once (slots); 0 -> 64 (see tick_depth) */
   int32_t max_tick_poses;     /* poses packed into one tick; 0 -> 4096 (also the largest B accepted) */
   int32_t use_cuda_graph;     /* nonzero: replay the tick's three launches from a captured graph */
