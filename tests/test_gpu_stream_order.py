@@ -87,3 +87,52 @@ def test_rewalk_gradient_and_backprojection_in_one_stream(drr):
     # the back-projection accumulates with atomics: equal up to the order of the adds
     scale = float(gv_ref.abs().max())
     assert float((gv - 2.0 * gv_ref).abs().max()) <= 1e-5 * scale
+
+
+def test_calls_from_several_threads_on_their_own_streams(drr):
+    # four host threads, each with its own stream, render and differentiate at once
+    # (the library's per-device launch caches and stream-ordered scratch are shared):
+    # every result equals the same call made alone
+    import threading
+    shape, sp = (40, 96, 80), (1.4, 1.2, 3.1)
+    vol = drr.Volume(inputs.ct_phantom_hu(shape, sp, seed=92), sp, hu=True)
+    det = inputs.Detector(420.0, 45, 61, 2.4, 2.1)
+    work = [(torch.from_numpy(inputs.random_poses(1 + i % 3, seed=300 + i)).cuda(),
+             torch.from_numpy(inputs.upstream_grad((1 + i % 3, 45, 61), seed=400 + i)).cuda()) for i in range(4)]
+    ref = []
+    for P, g in work:
+        E, J = drr.render(vol, det, P, jacobian=True)
+        ref.append((E.cpu().numpy(), drr.render_backward(vol, det, P, g, jac=J).cpu().numpy(),
+                    drr.render_backward(vol, det, P, g).cpu().numpy()))
+    torch.cuda.synchronize()
+    got = [None] * 4
+    errors = []
+
+    def run(i):
+        try:
+            P, g = work[i]
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                out = []
+                for _ in range(5):
+                    E, J = drr.render(vol, det, P, jacobian=True, stream=s)
+                    G = drr.render_backward(vol, det, P, g, jac=J, stream=s)
+                    Gw = drr.render_backward(vol, det, P, g, stream=s)
+                    out.append((E, G, Gw))
+                s.synchronize()
+                got[i] = [(E.cpu().numpy(), G.cpu().numpy(), Gw.cpu().numpy()) for E, G, Gw in out]
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=120)
+    assert not errors, errors
+    for i in range(4):
+        for E, G, Gw in got[i]:
+            np.testing.assert_array_equal(E, ref[i][0])
+            np.testing.assert_array_equal(G, ref[i][1])
+            np.testing.assert_array_equal(Gw, ref[i][2])
+    drr.stream_check()
