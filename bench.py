@@ -1016,7 +1016,7 @@ def main():
     ap.add_argument("--no-landscape", action="store_true")
     ap.add_argument("--no-vgs", action="store_true", help="skip the vectorised-tensor Siddon context line")
     ap.add_argument("--no-baselines", action="store_true",
-                    help="skip the L2 probe and the FD, plain-FP32 and vectorised baselines")
+                    help="skip the FD, plain-FP32, volume-adjoint and vectorised baselines (the L2 probe always runs)")
     ap.add_argument("--no-precision", action="store_true", help="skip the 512^3 precision-sweep workload")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds per served load level")
     args = ap.parse_args()
