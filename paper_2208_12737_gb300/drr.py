@@ -494,7 +494,9 @@ class Arena:
 
 
 class Ticket:
-    """A submitted request: owns its host buffers until wait() returns."""
+    """A submitted request.  Its host buffers (and its volume) are held by the server
+    object until wait() returns the request's result, so dropping a ticket that was
+    never waited for cannot free memory the request loop still writes into."""
 
     def __init__(self, server, tid, out, grad_pose, keep, loss=None):
         self.server = server
@@ -512,6 +514,7 @@ class Ticket:
             raise DrrError(st, self.server._lib.drr_last_error().decode())
         self.result = res
         self._keep = None
+        self.server._live.pop(self.id, None)  # the request is finished and released
         if st != 0:
             raise DrrError(st, self.server._lib.drr_last_error().decode())
         if self.loss is not None:
@@ -545,6 +548,7 @@ class Server:
                                 1 if use_cuda_graph else 0, device, int(max_tick_work),
                                 1 if plain_fp32_baseline else 0, int(tick_depth), int(spin_poll_us))
         self.h = ctypes.c_void_p()
+        self._live = {}  # ticket id -> the buffers and volume of a request not yet waited for
         check(self._lib.drr_server_create(ctypes.byref(cfg), ctypes.byref(self.h)))
 
     def submit(self, volume: Volume, det, poses, grad=None, fixed=None, eps: float = 1e-8, out=None) -> Ticket:
@@ -582,6 +586,7 @@ class Server:
             req.zncc_eps = float(eps)
         tid = ctypes.c_uint64()
         check(self._lib.drr_server_submit(self.h, ctypes.byref(req), ctypes.byref(tid)))
+        self._live[tid.value] = keep + [volume]
         return Ticket(self, tid.value, out, gpose, keep, loss)
 
     def pause(self, paused: bool = True):
@@ -595,8 +600,9 @@ class Server:
 
     def close(self):
         if self.h is not None and self.h.value:
-            check(self._lib.drr_server_destroy(self.h))
+            check(self._lib.drr_server_destroy(self.h))  # every request has finished or been cancelled
             self.h = ctypes.c_void_p()
+            self._live.clear()
 
     def __del__(self):
         try:

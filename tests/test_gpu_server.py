@@ -417,6 +417,27 @@ def test_caller_result_buffers(drr, vols):
     srv.close()
 
 
+def test_dropped_ticket_keeps_its_buffers_alive(drr, vols):
+    # a ticket dropped before its request ran: the server object keeps the request's
+    # buffers (and volume) until the server is closed, so the loop never writes into
+    # freed memory
+    import gc
+    data, sp, vol = vols["a"]
+    det = inputs.Detector(300.0, 30, 30, 1.5, 1.5)
+    srv = drr.Server(device_budget=64 << 20)
+    srv.pause(True)
+    t = srv.submit(vol, det, inputs.random_poses(1, seed=470), inputs.upstream_grad((1, 30, 30), seed=471))
+    tid = t.id
+    del t
+    gc.collect()
+    srv.pause(False)
+    E, _ = srv.submit(vol, det, inputs.random_poses(1, seed=472)).wait(20000)
+    assert np.isfinite(E).all()
+    assert tid in srv._live
+    srv.close()
+    assert not srv._live
+
+
 def test_tick_work_cap_bounds_each_tick(drr, vols):
     # a cap of about two requests' work per tick: a backlog of equal requests goes
     # into ticks of at most two, a request larger than the cap alone, and every
