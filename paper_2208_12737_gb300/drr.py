@@ -262,8 +262,9 @@ class Volume:
 def render(volume: Volume, det, poses, jacobian: bool = False, out=None, jac=None, stream=None):
     """E (B, H, W) float32; with jacobian=True also dE/d eta (B, 6, H, W).  poses, out and
     jac may be CUDA tensors or pinned CPU tensors (the kernels read and write those in
-    place); outputs not given are allocated on the poses' device (the current CUDA device
-    for pinned poses)."""
+    place: keep a pinned tensor alive, and read it, only after the stream's work is done,
+    e.g. after torch.cuda.synchronize()); outputs not given are allocated on the poses'
+    device (the current CUDA device for pinned poses)."""
     import torch
     lib = load()
     d = detector(det)
