@@ -15,9 +15,10 @@
  *      E = |p - s| * sum_m (alpha_{m+1} - alpha_m) V[voxel at the segment midpoint],
  *    with alpha clipped to the volume (Sec. 2.3) and clamped to [0, 1].
  *  - Volumes are passed x fastest: a C array of shape (nz, ny, nx).
- *  - Pointers named *_dev are caller-owned CUDA device memory on the current
- *    device; the library never frees them.  Host pointers are only read during
- *    the call.
+ *  - Pointers named *_dev are caller-owned buffers the kernels access: device
+ *    memory of the current device, or mapped page-locked host memory (see
+ *    "Buffers" below; each is checked before any launch).  The library never
+ *    frees them.  Other host pointers are only read during the call.
  *  - Calls taking a `cuda_stream` (a cudaStream_t, NULL = legacy default
  *    stream) enqueue their work on it and return without synchronising.
  *    Argument errors are reported synchronously; errors raised by device work
@@ -272,7 +273,7 @@ drr_status drr_render_plain_fp32(drr_volume v, const drr_detector* det, const fl
  * sink_dev: one float the kernel may write.  Errors: DRR_ERR_INVALID, DRR_ERR_CUDA. */
 drr_status drr_probe_l2_read(const void* buf_dev, size_t bytes, int32_t reps, float* sink_dev, void* cuda_stream);
 
-/* ---- serving: continuous batching of render / render+gradient requests ---- */
+/* ---- serving: continuous batching of renders, gradients, registration steps ---- */
 /* No counterpart in the paper (whose method is a library call); this is the
  * request loop of the serving workload.  A host thread forms "ticks": it admits
  * queued requests while slots and the explicit memory budgets allow, stages
