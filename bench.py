@@ -450,18 +450,82 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
                      "what": "drr_server with plain_fp32_baseline: one request per tick, plain FP32 forward walk, "
                              "gradients by central differences (13 renders per pose); same request mix"}
     reg = registration_step_latency(drr, vols)
+    lone = lone_request_latency(drr, vols)
     return {"p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "mean_ms": head["mean_ms"],
             "requests": head["requests"], "offered_rate_per_s": head["offered_rate_per_s"],
             "achieved_drrs_per_s": head["achieved_drrs_per_s"], "saturation_drrs_per_s": sat_rate,
             "saturation_p50_ms": float(np.percentile(lat_sat, 50)), "saturation_passes_per_s": rates,
             "ticks": head["ticks"],
             "gpu_busy_frac": head["gpu_busy_frac"], "by_load": runs, "plain_fp32_server": plain_res,
-            "registration_step": reg,
+            "registration_step": reg, "lone_requests": lone,
             "max_tick_work": max_tick_work,
             "tick_depth": tick_depth or 3,
             "workload": "8 resident volumes {128^3, 256^3, 512x512x133, 512x512x300} x {FP32, BF16}; one pose per "
                         "request; detector H=W~U{128..512} at 280/H mm, SDR 510; 50% render+pose-grad; Poisson "
                         "arrivals at the listed fractions of the measured saturation rate (headline: 50%)"}
+
+
+def lone_request_latency(drr, vols, sizes=(128, 256, 512), reps=20):
+    """One request at a time on the 256^3 FP32 volume: the direct calls' device time
+    (CUDA events around the call, pose setup included; the fwd+grad call takes the split
+    walk where it applies) and the served submit->result latency, with the loop sleeping
+    until woken (the default) and with spin_poll_us = 500."""
+    import torch
+    from paper_2208_12737_gb300 import inputs
+    vol = dict(vols)["256^3/f32"]
+    out = {}
+    for n in sizes:
+        det = inputs.Detector(510.0, n, n, 280.0 / n, 280.0 / n)
+        P_np = inputs.random_poses(1, seed=5)
+        P = torch.from_numpy(P_np).cuda()
+        g = torch.from_numpy(inputs.upstream_grad((1, n, n), seed=n)).cuda()
+        E = torch.empty((1, n, n), device="cuda")
+        J = torch.empty((1, 6, n, n), device="cuda")
+
+        def fwd():
+            drr.render(vol, det, P, out=E)
+
+        def fwdgrad():
+            drr.render(vol, det, P, jacobian=True, out=E, jac=J)
+            drr.render_backward(vol, det, P, g, jac=J)
+
+        row = {}
+        for name, fn in (("direct_render_ms", fwd), ("direct_render_pose_grad_ms", fwdgrad)):
+            for _ in range(5):
+                fn()
+            ms = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            row[name] = statistics.median(ms)
+        buf = np.zeros((1, n, n), np.float32)
+        for name, spin in (("served_render_ms", 0), ("served_render_spin_poll_ms", 500)):
+            srv = drr.Server(device_budget=256 << 20, spin_poll_us=spin)
+            lat = []
+            for i in range(reps + 5):
+                t = srv.submit(vol, det, P_np, out=buf)
+                t.wait(60000)
+                if i >= 5:
+                    lat.append(t.result.latency_ms)
+            srv.close()
+            row[name] = statistics.median(lat)
+        out[f"{n}x{n}"] = row
+    out["workload"] = "256^3 ellipsoid phantom (FP32, 1 mm), one pose per request, n x n detector at 280/n mm, SDR 510"
+    return out
+
+
+def run_lone_only():
+    """The lone-request latencies on their own (only the 256^3 volume resident)."""
+    from paper_2208_12737_gb300 import build, inputs
+    build.build()
+    from paper_2208_12737_gb300 import drr
+    v = inputs.ellipsoid_phantom((256, 256, 256), (1.0, 1.0, 1.0), seed=82, semi_range=(10, 60),
+                                 density_range=(0.0, 0.01))
+    return {"lone_requests": lone_request_latency(drr, [("256^3/f32", drr.Volume(v, (1.0, 1.0, 1.0)))])}
 
 
 def registration_step_latency(drr, vols, n=256, reps=20):
@@ -1019,9 +1083,14 @@ def main():
                     help="skip the FD, plain-FP32, volume-adjoint and vectorised baselines (the L2 probe always runs)")
     ap.add_argument("--no-precision", action="store_true", help="skip the 512^3 precision-sweep workload")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds per served load level")
+    ap.add_argument("--lone-only", action="store_true",
+                    help="only the lone-request latencies (one JSON object; a small case for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.lone_only:
+        print(json.dumps(run_lone_only()), flush=True)
+        return
     rank, world, local_rank = resolve_world(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
