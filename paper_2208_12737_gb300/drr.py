@@ -599,6 +599,13 @@ class Server:
         check(self._lib.drr_server_get_stats(self.h, ctypes.byref(st)))
         return {f: getattr(st, f) for f, _ in drr_server_stats._fields_}
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def close(self):
         if self.h is not None and self.h.value:
             check(self._lib.drr_server_destroy(self.h))  # every request has finished or been cancelled

@@ -404,17 +404,17 @@ def test_caller_result_buffers(drr, vols):
     data, sp, vol = vols["c"]
     det = inputs.Detector(300.0, 21, 26, 1.5, 1.5)
     P = inputs.random_poses(2, seed=460)
-    srv = drr.Server(device_budget=64 << 20)
-    mine = np.full((2, 21, 26), -7.0, np.float32)
-    E1, _ = srv.submit(vol, det, P, out=mine).wait(20000)
-    E2, _ = srv.submit(vol, det, P).wait(20000)
-    assert E1 is mine
-    np.testing.assert_array_equal(mine, E2)
-    for bad in (np.zeros((2, 21, 25), np.float32), np.zeros((2, 21, 26), np.float64),
-                np.zeros((2, 26, 21), np.float32).transpose(0, 2, 1)):
-        with pytest.raises(ValueError):
-            srv.submit(vol, det, P, out=bad)
-    srv.close()
+    with drr.Server(device_budget=64 << 20) as srv:
+        mine = np.full((2, 21, 26), -7.0, np.float32)
+        E1, _ = srv.submit(vol, det, P, out=mine).wait(20000)
+        E2, _ = srv.submit(vol, det, P).wait(20000)
+        assert E1 is mine
+        np.testing.assert_array_equal(mine, E2)
+        for bad in (np.zeros((2, 21, 25), np.float32), np.zeros((2, 21, 26), np.float64),
+                    np.zeros((2, 26, 21), np.float32).transpose(0, 2, 1)):
+            with pytest.raises(ValueError):
+                srv.submit(vol, det, P, out=bad)
+    assert not srv.h.value  # closed on leaving the block
 
 
 def test_dropped_ticket_keeps_its_buffers_alive(drr, vols):
