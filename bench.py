@@ -398,6 +398,7 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
             submit(srv, r).wait(120000)
         lat = []
         queue = []
+        queued = []  # submit -> admission into a tick, per request
         lock = threading.Condition()
         done_flag = [False]
 
@@ -411,6 +412,7 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
                     t = queue.pop(0)
                 t.wait(120000)
                 lat.append(t.result.latency_ms)
+                queued.append(t.result.queue_ms)
 
         th = threading.Thread(target=waiter)
         th.start()
@@ -433,7 +435,9 @@ def serve_bench(drr, hu133, seconds=2.0, seed=8, sat_requests=2000, loads=(0.25,
         return {"load": frac, "offered_rate_per_s": rate, "requests": int(n_req),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "achieved_drrs_per_s": n_req / wall, "ticks": int(st["ticks"]),
-                "gpu_busy_frac": st["gpu_busy_ms"] / 1e3 / wall}
+                "gpu_busy_frac": st["gpu_busy_ms"] / 1e3 / wall,
+                "queue_p50_ms": float(np.percentile(queued, 50)), "queue_p99_ms": float(np.percentile(queued, 99)),
+                "max_ms": float(lat.max())}
 
     runs = [poisson(f) for f in loads]
     head = next((r for r in runs if r["load"] == 0.5), runs[0])
